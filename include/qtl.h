@@ -1,0 +1,203 @@
+/*
+ * qtl.h -- C ABI of the GB300 Lindblad / quantum-trajectory solver library.
+ *
+ * The library integrates
+ *   - the Lindblad master equation (paper Sec. 3.2, the equation for d rho/dt
+ *     and the Lindblad dissipator D[C] rho = C rho C^dag - 1/2 {C^dag C, rho}),
+ *     with expectation values Tr(O_k rho(t)) at the times of tlist (Sec. 3.1,
+ *     sol.expect), and
+ *   - the Monte-Carlo wave-function method (Sec. 3.3: evolution under
+ *     H_eff = H - i/2 sum_k C_k^dag C_k, a jump when the squared norm falls
+ *     below a uniform threshold, channel k drawn with weight |C_k psi|^2),
+ * with an adaptive embedded Runge-Kutta 5(4) pair (Dormand-Prince 1980 or
+ * Tsitouras 2011) and a PI step-size controller.  The paper leaves the
+ * integrator to DifferentialEquations.jl (Sec. 2); the readings fixed here
+ * (error norm, controller constants, exact landing on tlist) are listed in
+ * the design notes and implemented identically by the test oracle.
+ *
+ * Conventions for every entry point:
+ *   - complex numbers are interleaved {re, im} FP64 (qtl_c128);
+ *   - dense matrices are column-major; a density matrix is passed as its
+ *     column-stacked vector vec(rho)[i + n*j] = rho[i][j];
+ *   - the caller owns every buffer it passes; inputs are copied (system
+ *     creation) or only read; outputs are caller-allocated;
+ *   - errors are returned as qtl_status; nothing aborts the process.  A
+ *     solve that cannot finish (step-size underflow, max_steps, a non-finite
+ *     error estimate) returns QTL_ESTEP and leaves the outputs it had not
+ *     reached untouched.
+ *   - functions ending in _async take DEVICE pointers, enqueue the work on
+ *     opts->cuda_stream and return at once; the status and counters of the
+ *     solve are written to the caller's device-resident qtl_device_info when
+ *     the work completes.  All other entry points take HOST pointers and
+ *     return when the results are in the caller's buffers.
+ */
+#ifndef QTL_H
+#define QTL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    double re, im;
+} qtl_c128;
+
+typedef enum {
+    QTL_OK = 0,
+    QTL_EINVAL = 1,   /* malformed argument (CSR structure, sizes, NaN/Inf, tlist order) */
+    QTL_ENOMEM = 2,   /* device allocation failed or an HBM budget would be exceeded */
+    QTL_ESTEP = 3,    /* step size below dt_min, max_steps reached, or non-finite error */
+    QTL_ECUDA = 4,    /* CUDA runtime error (message via qtl_last_cuda_error) */
+    QTL_ECANCEL = 5,  /* request cancelled */
+    QTL_EBUSY = 6,    /* result not ready yet */
+    QTL_ETOOBIG = 7   /* problem size outside what the selected kernel supports */
+} qtl_status;
+
+/* One operator: CSR (is_csr = 1: row_ptr[n+1], col_idx[nnz], vals[nnz], rows
+ * sorted or not, duplicates summed) or dense (is_csr = 0: vals[n*n]
+ * column-major; row_ptr/col_idx ignored).  Exact zeros are dropped. */
+typedef struct {
+    int32_t n;
+    int32_t is_csr;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col_idx;
+    const qtl_c128* vals;
+} qtl_op;
+
+enum { QTL_DP5 = 0, QTL_TSIT5 = 1 };
+enum { QTL_FP64 = 0, QTL_MIXED = 1 };
+
+/* Solver options.
+ *   method    QTL_DP5 | QTL_TSIT5
+ *   precision QTL_FP64: every operation in FP64.
+ *             QTL_MIXED: right-hand side and stage sums in FP32 (complex64
+ *             operator copies), state y and its update, error-norm
+ *             reduction, controller, jump logic and renormalisation in FP64.
+ *   rtol, atol    error-norm tolerances (rtol > 0, atol >= 0)
+ *   dt0           starting step; 0 selects the Hairer-Norsett-Wanner heuristic
+ *   dt_min        a rejected step that would shrink below dt_min fails (QTL_ESTEP)
+ *   max_steps     attempted steps per solve (per trajectory for mcsolve)
+ *   fixed_step    1: every step has size min(dt_fixed, time to the next
+ *                 tlist point) and is accepted without error control
+ *   cuda_stream   cudaStream_t to run on; NULL = the legacy default stream */
+typedef struct {
+    int32_t method;
+    int32_t precision;
+    double rtol;
+    double atol;
+    double dt0;
+    double dt_min;
+    int64_t max_steps;
+    int32_t fixed_step;
+    int32_t cluster_size; /* mesolve: CTAs per solve (0 = automatic, 1..16) */
+    double dt_fixed;
+    void* cuda_stream;
+} qtl_opts;
+
+/* Counters of one solve (summed over trajectories for mcsolve). */
+typedef struct {
+    int64_t steps_acc;
+    int64_t steps_rej;
+    int64_t rhs_evals;
+    int64_t jumps;
+} qtl_stats;
+
+/* Device-resident status of an _async solve: status is a qtl_status. */
+typedef struct {
+    int32_t status;
+    int32_t pad;
+    int64_t steps_acc;
+    int64_t steps_rej;
+    int64_t rhs_evals;
+    int64_t jumps;
+} qtl_device_info;
+
+typedef struct qtl_system qtl_system;
+
+/* Fills opts with the defaults: Tsit5, FP64, rtol 1e-8, atol 1e-10, automatic
+ * dt0, dt_min 0, max_steps 10^7, adaptive, automatic cluster size, default stream. */
+void qtl_opts_default(qtl_opts* opts);
+
+/* Builds a system (paper Sec. 3.2 / 3.3 inputs: H, c_ops, e_ops) on the
+ * current CUDA device.  The operators are copied; the caller may free them on
+ * return.  All operators must have the same dimension n (1 <= n <= 46340).
+ * The library forms, in FP64 on the host:
+ *   A = -i H - 1/2 sum_k C_k^dag C_k   (so -i H_eff psi = A psi, Sec. 3.3),
+ *   B =  i H - 1/2 sum_k C_k^dag C_k,
+ *   L = I kron A + B^T kron I + sum_k conj(C_k) kron C_k  (column stacking,
+ *       the Liouvillian of Sec. 3.2; built on first use by a mesolve),
+ * and uploads FP64 and complex64 copies to device memory.
+ * Errors: QTL_EINVAL (bad structure, mismatched n, NaN/Inf, n_c or n_e < 0 or
+ * > 64), QTL_ENOMEM, QTL_ECUDA.  *out is NULL on error. */
+qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c,
+                             const qtl_op* e_ops, int32_t n_e, qtl_system** out);
+
+/* Releases the system and its device memory (NULL is a no-op).  Work enqueued
+ * by _async calls on the system must have completed. */
+void qtl_system_free(qtl_system* sys);
+
+/* Hilbert dimension, number of collapse operators / observables, and the
+ * number of stored entries of the Liouvillian (0 before it is built). */
+int32_t qtl_system_dim(const qtl_system* sys);
+int64_t qtl_system_liouvillian_nnz(const qtl_system* sys);
+
+/* mesolve (Sec. 3.2): integrates d rho/dt = L rho from tlist[0].
+ *   state0    is_ket = 1: psi0[n] (rho0 = |psi0><psi0|, ket2dm);
+ *             is_ket = 0: vec(rho0)[n*n] column-major.
+ *   tlist[nt] non-decreasing, finite, nt >= 1; steps land exactly on each time.
+ *   expect_out[n_e*nt] (row k = e_op k): Tr(O_k rho(tlist[t])); may be NULL if n_e = 0.
+ *   states_out NULL, or [nt*n*n]: vec(rho(tlist[t])) for each t.
+ *   stats      NULL or filled.
+ * Host pointers; returns when done.  QTL_ETOOBIG when n*n exceeds the
+ * cluster kernel's capacity (65536 entries). */
+qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket,
+                       const double* tlist, int32_t nt, const qtl_opts* opts,
+                       qtl_c128* expect_out, qtl_c128* states_out, qtl_stats* stats);
+
+/* Same as qtl_mesolve with device pointers, enqueued on opts->cuda_stream.
+ * Scratch is taken stream-ordered from the device's default memory pool and
+ * returned on the same stream.  Argument errors found on the host are
+ * returned directly; errors found by the kernel (tlist order, step failure)
+ * land in info->status. */
+qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_t is_ket,
+                             const double* tlist_dev, int32_t nt, const qtl_opts* opts,
+                             qtl_c128* expect_dev, qtl_c128* states_dev,
+                             qtl_device_info* info_dev);
+
+/* mcsolve (Sec. 3.3): ntraj trajectories from the ket psi0[n].
+ *   seed      64-bit key of the per-trajectory Philox4x32-10 streams: draw d
+ *             of trajectory j uses counter (d, traj_offset + j, 0, 0) and key
+ *             (seed & 0xffffffff, seed >> 32); draws alternate threshold,
+ *             channel, threshold, ...
+ *   expect_out[n_e*nt]: the trajectory mean of <psi|O_k|psi>/<psi|psi>.
+ *   traj_expect_out NULL, or [n_e*nt*ntraj] laid out [(k*nt + t)*ntraj + j].
+ * Host pointers; returns when done. */
+qtl_status qtl_mcsolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                       int32_t ntraj, uint64_t seed, int64_t traj_offset, const qtl_opts* opts,
+                       qtl_c128* expect_out, qtl_c128* traj_expect_out, qtl_stats* stats);
+
+/* Same with device pointers, enqueued on opts->cuda_stream (see
+ * qtl_mesolve_async).  traj_expect_dev may be NULL (scratch is used). */
+qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const double* tlist_dev,
+                             int32_t nt, int32_t ntraj, uint64_t seed, int64_t traj_offset,
+                             const qtl_opts* opts, qtl_c128* expect_dev,
+                             qtl_c128* traj_expect_dev, qtl_device_info* info_dev);
+
+/* Human-readable text of a status, and the last CUDA error seen by this
+ * thread (empty string if none). */
+const char* qtl_strerror(qtl_status s);
+const char* qtl_last_cuda_error(void);
+
+/* Number of kernel launches the library has issued in this process
+ * (a monotone counter, for accounting in benchmarks). */
+int64_t qtl_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTL_H */

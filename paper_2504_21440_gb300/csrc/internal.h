@@ -1,0 +1,130 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qtl.h"
+
+namespace qtl {
+
+// ---------------------------------------------------------------- host CSR
+struct Csr {
+    int n = 0;
+    std::vector<int32_t> rp;   // n+1
+    std::vector<int32_t> ci;   // nnz
+    std::vector<double> re, im;
+    int64_t nnz() const { return (int64_t)ci.size(); }
+};
+
+// ------------------------------------------------------ device CSR copies
+// Rows are stored with their entries grouped as [real-only | imaginary-only |
+// complex]; seg[r] = {start, start of imaginary-only, start of complex, end},
+// so a product spends 2 FMAs on an entry that is purely real or imaginary.
+struct DevCsr {
+    int n = 0;
+    int64_t nnz = 0;
+    int4* seg = nullptr;
+    int32_t* rp = nullptr;
+    int32_t* ci = nullptr;
+    double2* v64 = nullptr;
+    float2* v32 = nullptr;
+};
+
+// ---------------------------------------------------------------- system
+struct System {
+    int n = 0, n_c = 0, n_e = 0;
+    Csr H;
+    std::vector<Csr> C;   // collapse operators
+    std::vector<Csr> O;   // observables
+    Csr A;                // -i H - 1/2 sum C^dag C
+    Csr Bt;               // (i H - 1/2 sum C^dag C)^T
+    // device
+    DevCsr dA;            // mcsolve RHS
+    DevCsr dC;            // all collapse operators stacked: rows k*n .. k*n+n-1
+    DevCsr dO;            // all observables stacked: rows k*n .. k*n+n-1
+    DevCsr dL;            // Liouvillian (built lazily)
+    std::vector<int32_t> L_rp;  // host copy of its row pointers (shared-memory sizing)
+    double2* ew = nullptr;      // [n*n][n_e] trace weights (built with the Liouvillian)
+    int device = 0;
+};
+
+// -------------------------------------------- device-side solve descriptors
+struct MeJob {
+    int n, L;
+    const int4* seg;      // Liouvillian, segmented rows
+    const int32_t* ci;
+    const double2* lv64;
+    const float2* lv32;
+    int n_e;
+    const double2* ew;    // [L][n_e]: Tr(O_e rho) = sum_r ew[r][e] * vec(rho)[r]
+    const double* tlist;
+    int nt;
+    const double2* state0;
+    int is_ket;
+    double* epart;        // scratch [nt][C][2 n_e]: per-CTA partial expectation values
+    double2* expect;      // [n_e*nt]
+    double2* states;      // [nt*L] or null
+    qtl_device_info* info;
+    double rtol, atol, dt0, dt_min, dt_fixed;
+    long long max_steps;
+    int fixed;
+    int method;
+    int smem_nnz;         // per-CTA shared-memory capacity for Liouvillian entries
+};
+
+struct McJob {
+    int n;
+    int a_nnz;            // entries of A
+    int a_smem;           // 1: the kernel keeps A in shared memory
+    const int4* aseg;     // A = -i H_eff, segmented rows
+    const int32_t* arp;
+    const int32_t* aci;
+    const double2* av64;
+    const float2* av32;
+    int n_c;
+    const int32_t* crp;   // stacked collapse ops
+    const int32_t* cci;
+    const double2* cv;
+    int n_e;
+    const int32_t* orp;   // stacked observables
+    const int32_t* oci;
+    const double2* ov;
+    const double* tlist;
+    int nt;
+    const double2* psi0;
+    int ntraj;
+    unsigned long long seed;
+    long long traj_offset;
+    double2* traj_expect;  // [(k*nt + t)*ntraj + j]
+    double2* expect;       // [n_e*nt] (mean)
+    qtl_device_info* info;
+    double rtol, atol, dt0, dt_min, dt_fixed;
+    long long max_steps;
+    int fixed;
+    int method;
+};
+
+// kernels (launchers return cudaError_t of the launch)
+bool me_plan(int L_max, int cluster_size, int* C, int* rpt);
+int me_smem_nnz_budget(int precision, int rpt);
+cudaError_t launch_me_cluster(const MeJob* jobs_dev, int njobs, int L_max, int smem_nnz,
+                              int precision, int cluster_size, cudaStream_t st);
+cudaError_t launch_mc_traj(const McJob& job, int precision, cudaStream_t st);
+cudaError_t launch_mc_reduce(const McJob& job, cudaStream_t st);
+cudaError_t launch_info_init(qtl_device_info* info, cudaStream_t st);
+
+int me_cluster_capacity();        // max L handled by the cluster kernel
+int mc_traj_capacity();           // max n handled by the trajectory kernel
+
+void count_launch(int k = 1);
+void set_cuda_error(cudaError_t e);
+
+}  // namespace qtl
+
+struct qtl_system {
+    qtl::System s;
+};

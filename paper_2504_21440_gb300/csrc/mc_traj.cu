@@ -1,0 +1,811 @@
+// mcsolve: Monte-Carlo wave-function trajectories (paper Sec. 3.3).
+//
+// One CTA integrates one trajectory at a time (persistent loop over
+// trajectories): d psi/dt = A psi with A = -i H_eff = -i H - 1/2 sum C^dag C,
+// adaptive RK 5(4) with the PI controller, exact landing on tlist, a jump
+// when |psi|^2 drops below the trajectory's threshold r:
+//   * the crossing time inside the accepted step is located by the Illinois
+//     method on ln|psi(t+tau)|^2 - ln r, psi(t+tau) being one RK step of size
+//     tau from the step's start (stop at bracket < 1e-10 max(1,|t|) or after
+//     30 evaluations; the jump is taken at the last evaluated point);
+//   * channel k is the smallest with sum_{j<=k} |C_j psi|^2 >= u sum_j |C_j psi|^2;
+//   * psi <- C_k psi / |C_k psi| and a new threshold is drawn.
+// Uniforms come from Philox4x32-10 (Salmon et al., SC'11) with counter
+// (draw, trajectory, 0, 0) and key (seed lo, seed hi), converted with 52 bits.
+//
+// Thread t of the CTA owns rows i = t + m*T (m < RPT) of psi, y_new and
+// k_1..k_7 in registers; the stage input is staged in shared memory (two
+// alternating buffers) for the sparse A*psi product, and an FP64 copy of psi
+// is staged there for expectation values and jumps.  Sums are fixed-order
+// (warp shuffle tree, then warps in order), so a trajectory's result does not
+// depend on which CTA or batch it runs in.
+#include "internal.h"
+#include "rk.cuh"
+
+namespace qtl {
+
+constexpr int MC_TMAX = 256;
+
+template <bool MIXED>
+struct MPrec;
+template <>
+struct MPrec<false> {
+    using T = double;
+    using T2 = double2;
+};
+template <>
+struct MPrec<true> {
+    using T = float;
+    using T2 = float2;
+};
+
+__device__ __forceinline__ double2 to_d2_mc(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2_mc(float2 v) { return make_double2(v.x, v.y); }
+template <class T2>
+__device__ __forceinline__ T2 from_d2_mc(double2 v);
+template <>
+__device__ __forceinline__ double2 from_d2_mc<double2>(double2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 from_d2_mc<float2>(double2 v) {
+    return make_float2((float)v.x, (float)v.y);
+}
+
+// Values reduced at once: |psi|^2 and 2 per observable, or 1 per channel.
+__host__ __device__ __forceinline__ int mc_red_stride(int n_e, int n_c) {
+    int a = 2 + 2 * n_e;
+    return a > n_c ? a : n_c;
+}
+
+__device__ __forceinline__ float mc_warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double mc_warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct BlockReducer {
+    double* wred;  // [nw][rs]
+    double* out;   // [rs]
+    int rs, lane, warp, tid, nw;
+    __device__ void stage(int i, double v) {
+        v = mc_warp_sum(v);
+        if (lane == 0) wred[warp * rs + i] = v;
+    }
+    __device__ void finish(int nv) {
+        __syncthreads();
+        if (tid < nv) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += wred[w * rs + tid];
+            out[tid] = s;
+        }
+        __syncthreads();
+    }
+};
+
+// Philox4x32-10: ten rounds of the published round function; key bumped by
+// the Weyl constants between rounds.
+__device__ __forceinline__ double philox_uniform(unsigned long long seed, unsigned long long traj,
+                                                 unsigned draw) {
+    unsigned c0 = draw, c1 = (unsigned)traj, c2 = 0u, c3 = 0u;
+    unsigned k0 = (unsigned)(seed & 0xffffffffull), k1 = (unsigned)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        unsigned lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        unsigned lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    unsigned long long x = ((unsigned long long)c1 << 20) | (unsigned long long)(c0 >> 12);
+    return ((double)x + 0.5) * 0x1p-52;
+}
+
+// Row r of a segmented CSR (real-only | imaginary-only | complex entries)
+// times x held in shared memory.
+template <class T2, class TV>
+__device__ __forceinline__ T2 mc_spmv_row(int r, const int4* __restrict__ seg,
+                                          const int32_t* __restrict__ ci,
+                                          const TV* __restrict__ v, const T2* x) {
+    const int4 sg = __ldg(seg + r);
+    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
+    int p = sg.x;
+    for (; p < sg.y; ++p) {
+        const decltype(T2::x) a = __ldg(&v[p].x);
+        const T2 xv = x[__ldg(ci + p)];
+        ax = fma(a, xv.x, ax);
+        ay = fma(a, xv.y, ay);
+    }
+    for (; p < sg.z; ++p) {
+        const decltype(T2::x) b = __ldg(&v[p].y);
+        const T2 xv = x[__ldg(ci + p)];
+        bx = fma(-b, xv.y, bx);
+        by = fma(b, xv.x, by);
+    }
+    for (; p < sg.w; ++p) {
+        const TV a = __ldg(v + p);
+        const T2 xv = x[__ldg(ci + p)];
+        ax = fma(a.x, xv.x, ax);
+        ay = fma(a.x, xv.y, ay);
+        bx = fma(-a.y, xv.y, bx);
+        by = fma(a.y, xv.x, by);
+    }
+    T2 acc;
+    acc.x = ax + bx;
+    acc.y = ay + by;
+    return acc;
+}
+
+// A's row from the CTA's shared-memory copy (rows packed in CTA order).
+template <class T2, class TV>
+__device__ __forceinline__ T2 mc_spmv_row_s(int r, const int4* __restrict__ s_seg,
+                                            const int32_t* __restrict__ s_ci,
+                                            const TV* __restrict__ s_v, const T2* x) {
+    const int4 sg = s_seg[r];
+    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
+    int p = sg.x;
+#pragma unroll 4
+    for (; p < sg.y; ++p) {
+        const decltype(T2::x) a = s_v[p].x;
+        const T2 xv = x[s_ci[p]];
+        ax = fma(a, xv.x, ax);
+        ay = fma(a, xv.y, ay);
+    }
+#pragma unroll 4
+    for (; p < sg.z; ++p) {
+        const decltype(T2::x) b = s_v[p].y;
+        const T2 xv = x[s_ci[p]];
+        bx = fma(-b, xv.y, bx);
+        by = fma(b, xv.x, by);
+    }
+#pragma unroll 2
+    for (; p < sg.w; ++p) {
+        const TV a = s_v[p];
+        const T2 xv = x[s_ci[p]];
+        ax = fma(a.x, xv.x, ax);
+        ay = fma(a.x, xv.y, ay);
+        bx = fma(-a.y, xv.y, bx);
+        by = fma(a.y, xv.x, by);
+    }
+    T2 acc;
+    acc.x = ax + bx;
+    acc.y = ay + by;
+    return acc;
+}
+
+enum { MC_STEP = 0, MC_REPEAT = 1, MC_DONE = 2 };
+
+// Control block broadcast by thread 0 (scalar control in one thread: GB300's
+// FP64 pipe is 1/64 rate, so no FP64 scalar work is replicated per thread).
+struct McCtl {
+    double coef[28];  // htry * a_sj (21, packed by stage), htry * e_j (7)
+    double inv;       // 1 / |C_k psi*| of the chosen channel
+    int action, land, accept, save, ch, rootgo, pub;
+    float wf[MC_TMAX / 32];
+    double wd[MC_TMAX / 32];
+};
+
+__host__ __device__ constexpr int mc_coef_a(int s, int j) { return s * (s - 1) / 2 + j; }
+
+template <bool MIXED, int RPT, int MAXT>
+__global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
+    using T = typename MPrec<MIXED>::T;
+    using T2 = typename MPrec<MIXED>::T2;
+    using TV = T2;
+    extern __shared__ __align__(16) unsigned char mc_smem[];
+    __shared__ McCtl cb;
+    const int n = J.n;
+    const int tid = threadIdx.x, T_ = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = (T_ + 31) >> 5;
+    const int rs = mc_red_stride(J.n_e, J.n_c);
+    double2* yd = (double2*)mc_smem;
+    T2* ys0 = (T2*)(yd + n);
+    T2* ys1 = ys0 + n;
+    double* wred = (double*)(((uintptr_t)(ys1 + n) + 15) & ~(uintptr_t)15);
+    double* bout = wred + nw * rs;
+    BlockReducer red{wred, bout, rs, lane, warp, tid, nw};
+    const RkTab& tab = RK_TABS[J.method];
+    const TV* av = MIXED ? (const TV*)J.av32 : (const TV*)J.av64;
+    // A (constant, shared by every trajectory of this CTA) into shared memory
+    const bool cached = J.a_smem;
+    int4* s_seg = (int4*)(((uintptr_t)(bout + rs + 2) + 15) & ~(uintptr_t)15);
+    TV* s_v = (TV*)(s_seg + n);
+    int32_t* s_ci = (int32_t*)(s_v + J.a_nnz);
+    if (cached) {
+        for (int r = tid; r < n; r += T_) s_seg[r] = __ldg(J.aseg + r);
+        for (int p = tid; p < J.a_nnz; p += T_) {
+            s_v[p] = __ldg(av + p);
+            s_ci[p] = __ldg(J.aci + p);
+        }
+        __syncthreads();
+    }
+    auto rhs_row = [&](int r, const T2* x) -> T2 {
+        return cached ? mc_spmv_row_s<T2, TV>(r, s_seg, s_ci, s_v, x)
+                      : mc_spmv_row<T2, TV>(r, J.aseg, J.aci, av, x);
+    };
+
+    long long acc_steps = 0, rej_steps = 0, rhs_evals = 0, jumps = 0;  // thread 0
+    int status = QTL_OK;                                                 // thread 0
+
+    for (int jt = blockIdx.x; jt < J.ntraj; jt += gridDim.x) {
+        const unsigned long long traj = (unsigned long long)(J.traj_offset + jt);
+        double2 y[RPT], ynew[RPT];
+        T2 k[7][RPT];
+        bool own[RPT];
+        int row[RPT];
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            row[m] = tid + m * T_;
+            own[m] = row[m] < n;
+            y[m] = own[m] ? J.psi0[row[m]] : make_double2(0.0, 0.0);
+            ynew[m] = y[m];
+            if (own[m]) {
+                yd[row[m]] = y[m];
+                ys0[row[m]] = from_d2_mc<T2>(y[m]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < RPT; ++m)
+            if (own[m]) k[0][m] = rhs_row(row[m], ys0);
+
+        // <psi|O_e|psi>/<psi|psi> from the FP64 copy in yd (all rows written and
+        // synchronised by the caller); returns |psi|^2 in thread 0.
+        auto save = [&](int idx) -> double {
+            double s2 = 0.0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) s2 += y[m].x * y[m].x + y[m].y * y[m].y;
+            red.stage(0, s2);
+            for (int e = 0; e < J.n_e; ++e) {
+                double sr = 0.0, si = 0.0;
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    const int i = e * n + row[m];
+                    double ox = 0.0, oy = 0.0;
+                    for (int p = __ldg(J.orp + i); p < __ldg(J.orp + i + 1); ++p) {
+                        const double2 o = J.ov[p];
+                        const double2 v = yd[__ldg(J.oci + p)];
+                        ox += o.x * v.x - o.y * v.y;
+                        oy += o.x * v.y + o.y * v.x;
+                    }
+                    // conj(psi_i) * (O psi)_i
+                    sr += y[m].x * ox + y[m].y * oy;
+                    si += y[m].x * oy - y[m].y * ox;
+                }
+                red.stage(1 + 2 * e, sr);
+                red.stage(2 + 2 * e, si);
+            }
+            red.finish(1 + 2 * J.n_e);
+            if (tid < J.n_e) {
+                const double nn = bout[0];
+                J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] =
+                    make_double2(bout[1 + 2 * tid] / nn, bout[2 + 2 * tid] / nn);
+            }
+            return bout[0];
+        };
+        double norm2 = save(0);  // meaningful in thread 0
+
+        // thread-0 control state
+        double t = J.tlist[0], h = 0.0, htry = 0.0, t_target = 0.0, r = 0.0;
+        unsigned draw = 0;
+        int idx = 1;
+        long long attempts = 0;
+        CtlF ctl;
+        ctl.init();
+        if (tid == 0) {
+            r = philox_uniform(J.seed, traj, draw++);
+            rhs_evals += 1;
+        }
+        // ---- starting step ----
+        if (J.fixed) {
+            h = J.dt_fixed;
+        } else if (J.dt0 > 0.0) {
+            h = J.dt0;
+        } else {
+            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (!own[m]) continue;
+                const double2 f0 = to_d2_mc(k[0][m]);
+                const float a = sqrtf((float)(y[m].x * y[m].x + y[m].y * y[m].y));
+                const float sc = (float)J.atol + (float)J.rtol * a;
+                const float q0 = a / sc, q1 = sqrtf((float)(f0.x * f0.x + f0.y * f0.y)) / sc;
+                s0 += (double)(q0 * q0);
+                s1 += (double)(q1 * q1);
+            }
+            red.stage(0, s0);
+            red.stage(1, s1);
+            red.finish(2);
+            const double d0 = sqrt(bout[0] / n), d1 = sqrt(bout[1] / n);
+            const double h0 = start_h0(d0, d1);
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (!own[m]) continue;
+                const double2 f0 = to_d2_mc(k[0][m]);
+                ys1[row[m]] = from_d2_mc<T2>(make_double2(y[m].x + h0 * f0.x, y[m].y + h0 * f0.y));
+            }
+            __syncthreads();
+            double s2 = 0.0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (!own[m]) continue;
+                const double2 f1 = to_d2_mc(rhs_row(row[m], ys1));
+                const double2 f0 = to_d2_mc(k[0][m]);
+                const float sc = (float)J.atol + (float)J.rtol * sqrtf((float)(y[m].x * y[m].x + y[m].y * y[m].y));
+                const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
+                const float q = sqrtf(dx * dx + dy * dy) / sc;
+                s2 += (double)(q * q);
+            }
+            red.stage(0, s2);
+            red.finish(1);
+            if (tid == 0) {
+                rhs_evals += 1;
+                h = start_h(h0, d1, sqrt(bout[0] / n) / h0);
+            }
+        }
+
+        auto next_action = [&]() {
+            cb.pub = 0;
+            for (;;) {
+                if (status != QTL_OK || idx >= J.nt) {
+                    cb.action = MC_DONE;
+                    return;
+                }
+                t_target = J.tlist[idx];
+                if (!(t_target >= J.tlist[idx - 1]) || !isfinite(t_target)) {
+                    status = QTL_EINVAL;
+                    continue;
+                }
+                if (!(t < t_target)) {
+                    cb.action = MC_REPEAT;
+                    cb.save = idx++;
+                    return;
+                }
+                if (attempts >= J.max_steps) {
+                    status = QTL_ESTEP;
+                    continue;
+                }
+                ++attempts;
+                const bool land = lands(h, t, t_target);
+                htry = land ? (t_target - t) : h;
+                cb.land = land;
+                cb.action = MC_STEP;
+                cb.coef[27] = htry;
+                cb.pub = 1;
+                return;
+            }
+        };
+        // warp 0: htry * (a_sj, e_j) in FP64, one product per lane, when
+        // thread 0 has set cb.pub (read after the warp barrier)
+        auto publish_coefs = [&]() {
+            __syncwarp();
+            if (cb.pub) {
+                const double hh = cb.coef[27];
+                __syncwarp();
+                if (lane < 21) {
+                    int s = 1, j = lane;
+                    while (j >= s) {
+                        j -= s;
+                        ++s;
+                    }
+                    cb.coef[lane] = hh * tab.a[s][j];
+                } else if (lane < 28) {
+                    cb.coef[lane] = hh * tab.e[lane - 21];
+                }
+            }
+            __syncwarp();
+        };
+        // One RK step of size h (coefficients in cb.coef) from (y, k1): k[1..6], ynew.
+        auto rk_step = [&]() {
+#pragma unroll
+            for (int s = 1; s < 7; ++s) {
+                T2* ysb = (s & 1) ? ys0 : ys1;
+                T ha[6];
+#pragma unroll
+                for (int j = 0; j < 6; ++j) ha[j] = j < s ? (T)cb.coef[mc_coef_a(s, j)] : (T)0;
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    T ax = 0, ay = 0;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        if (j < s) {
+                            ax = fma(ha[j], k[j][m].x, ax);
+                            ay = fma(ha[j], k[j][m].y, ay);
+                        }
+                    }
+                    T2 o;
+                    if (s == 6) {
+                        ynew[m] = make_double2(y[m].x + (double)ax, y[m].y + (double)ay);
+                        o = from_d2_mc<T2>(ynew[m]);
+                    } else {
+                        o.x = (T)y[m].x + ax;
+                        o.y = (T)y[m].y + ay;
+                    }
+                    ysb[row[m]] = o;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int m = 0; m < RPT; ++m)
+                    if (own[m]) k[s][m] = rhs_row(row[m], ysb);
+            }
+        };
+        // |ynew|^2 (FP64) and the FP32 error sum, warp -> thread 0.
+        auto reduce_step = [&](float se, double sn, float* S, double* N) {
+            se = mc_warp_sum_f(se);
+            sn = mc_warp_sum(sn);
+            if (lane == 0) {
+                cb.wf[warp] = se;
+                cb.wd[warp] = sn;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                float a = 0.f;
+                double b = 0.0;
+                for (int w = 0; w < nw; ++w) {
+                    a += cb.wf[w];
+                    b += cb.wd[w];
+                }
+                *S = a;
+                *N = b;
+            }
+        };
+        auto norm2_ynew = [&](double* N) {
+            double sn = 0.0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) sn += ynew[m].x * ynew[m].x + ynew[m].y * ynew[m].y;
+            float dummy;
+            reduce_step(0.f, sn, &dummy, N);
+        };
+
+        if (tid == 0) next_action();
+        if (warp == 0) publish_coefs();
+        __syncthreads();
+
+        // root-find state (thread 0)
+        double lo = 0.0, glo = 0.0, hi = 0.0, ghi = 0.0, tau = 0.0, log_r = 0.0;
+        int side = 0, it = 0;
+
+        for (;;) {
+            const int action = cb.action;
+            if (action == MC_DONE) break;
+            if (action == MC_REPEAT) {
+#pragma unroll
+                for (int m = 0; m < RPT; ++m)
+                    if (own[m]) yd[row[m]] = y[m];
+                __syncthreads();
+                const double nn = save(cb.save);
+                if (tid == 0) {
+                    norm2 = nn;
+                    next_action();
+                }
+                if (warp == 0) publish_coefs();
+                __syncthreads();
+                continue;
+            }
+            const bool land = cb.land;
+            rk_step();
+            float se = 0.f;
+            double sn = 0.0;
+            {
+                T he[7];
+#pragma unroll
+                for (int j = 0; j < 7; ++j) he[j] = (T)cb.coef[21 + j];
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    T ex = 0, ey = 0;
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) {
+                        ex = fma(he[j], k[j][m].x, ex);
+                        ey = fma(he[j], k[j][m].y, ey);
+                    }
+                    const float yx = (float)y[m].x, yy = (float)y[m].y;
+                    const float nx = (float)ynew[m].x, ny = (float)ynew[m].y;
+                    const float a2 = fmaxf(yx * yx + yy * yy, nx * nx + ny * ny);
+                    const float sc = (float)J.atol + (float)J.rtol * sqrtf(a2);
+                    const float fx = (float)ex, fy = (float)ey;
+                    se += (fx * fx + fy * fy) / (sc * sc);
+                    sn += ynew[m].x * ynew[m].x + ynew[m].y * ynew[m].y;
+                }
+            }
+            float S = 0.f;
+            double norm2_new = 0.0;
+            reduce_step(se, sn, &S, &norm2_new);
+            if (tid == 0) {
+                rhs_evals += 6;
+                const float err = sqrtf(S / (float)n);
+                int accept = 1;
+                float fac = 1.0f;
+                if (!J.fixed) {
+                    if (!(S <= (float)n)) {
+                        accept = 0;
+                        ++rej_steps;
+                        h = htry * (double)ctl.on_reject(err);
+                        if (h < J.dt_min || !isfinite(S)) status = QTL_ESTEP;
+                    } else {
+                        fac = ctl.on_accept(err);
+                    }
+                }
+                cb.save = -1;
+                cb.rootgo = 0;
+                if (accept) {
+                    ++acc_steps;
+                    const double h_next = J.fixed ? J.dt_fixed : htry * (double)fac;
+                    if (norm2_new >= r) {
+                        t = land ? t_target : t + htry;
+                        norm2 = norm2_new;
+                        h = h_next;
+                        if (land) cb.save = idx++;
+                    } else {
+                        // jump inside [t, t + htry]: Illinois on ln|psi|^2 - ln r
+                        accept = 2;
+                        h = h_next;
+                        log_r = log(r);
+                        lo = 0.0;
+                        glo = log(norm2) - log_r;
+                        hi = htry;
+                        ghi = log(norm2_new) - log_r;
+                        tau = hi;
+                        side = 0;
+                        it = 0;
+                        cb.pub = 0;
+                        if (!(hi - lo <= 1e-10 * fmax(1.0, fabs(t)))) {
+                            tau = (lo * ghi - hi * glo) / (ghi - glo);
+                            cb.rootgo = 1;
+                            cb.coef[27] = tau;
+                            cb.pub = 1;
+                        }
+                    }
+                }
+                cb.accept = accept;
+                if (accept != 2) next_action();
+            }
+            if (warp == 0) publish_coefs();
+            __syncthreads();
+            const int accept = cb.accept;
+            if (accept == 1) {
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    y[m] = ynew[m];
+                    k[0][m] = k[6][m];
+                }
+                const int sv = cb.save;
+                if (sv >= 0) {
+#pragma unroll
+                    for (int m = 0; m < RPT; ++m)
+                        if (own[m]) yd[row[m]] = y[m];
+                    __syncthreads();
+                    save(sv);
+                }
+                continue;
+            }
+            if (accept == 0) continue;
+            // ---- quantum jump: locate the crossing ----
+            while (cb.rootgo) {
+                rk_step();
+                double n2 = 0.0;
+                norm2_ynew(&n2);
+                if (tid == 0) {
+                    rhs_evals += 6;
+                    ++it;
+                    const double gv = log(n2) - log_r;
+                    int go = 1;
+                    if (gv > 0) {
+                        lo = tau;
+                        glo = gv;
+                        if (side == 1) ghi *= 0.5;
+                        side = 1;
+                    } else if (gv < 0) {
+                        hi = tau;
+                        ghi = gv;
+                        if (side == -1) glo *= 0.5;
+                        side = -1;
+                    } else {
+                        go = 0;
+                    }
+                    if (go && (it >= 30 || hi - lo <= 1e-10 * fmax(1.0, fabs(t)))) go = 0;
+                    if (go) {
+                        tau = (lo * ghi - hi * glo) / (ghi - glo);
+                        cb.coef[27] = tau;
+                    }
+                    cb.rootgo = go;
+                    cb.pub = go;
+                }
+                if (warp == 0) publish_coefs();
+                __syncthreads();
+            }
+            // psi* = ynew (last evaluated point); channel weights |C_c psi*|^2
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) yd[row[m]] = ynew[m];
+            __syncthreads();
+            for (int c = 0; c < J.n_c; ++c) {
+                double s = 0.0;
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    const int i = c * n + row[m];
+                    double vx = 0.0, vy = 0.0;
+                    for (int p = __ldg(J.crp + i); p < __ldg(J.crp + i + 1); ++p) {
+                        const double2 cv = J.cv[p];
+                        const double2 v = yd[__ldg(J.cci + p)];
+                        vx += cv.x * v.x - cv.y * v.y;
+                        vy += cv.x * v.y + cv.y * v.x;
+                    }
+                    s += vx * vx + vy * vy;
+                }
+                red.stage(c, s);
+            }
+            red.finish(J.n_c);
+            if (tid == 0) {
+                double total = 0.0;
+                for (int c = 0; c < J.n_c; ++c) total += bout[c];
+                const double u = philox_uniform(J.seed, traj, draw++);
+                int ch = J.n_c - 1;
+                double acc = 0.0;
+                for (int c = 0; c < J.n_c; ++c) {
+                    acc += bout[c];
+                    if (acc >= u * total) {
+                        ch = c;
+                        break;
+                    }
+                }
+                cb.ch = ch;
+                cb.inv = 1.0 / sqrt(bout[ch]);
+                r = philox_uniform(J.seed, traj, draw++);
+                t = t + tau;
+                ++jumps;
+                rhs_evals += 1;
+                next_action();
+            }
+            if (warp == 0) publish_coefs();
+            __syncthreads();
+            {
+                const int ch = cb.ch;
+                const double inv = cb.inv;
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    const int i = ch * n + row[m];
+                    double vx = 0.0, vy = 0.0;
+                    for (int p = __ldg(J.crp + i); p < __ldg(J.crp + i + 1); ++p) {
+                        const double2 cv = J.cv[p];
+                        const double2 v = yd[__ldg(J.cci + p)];
+                        vx += cv.x * v.x - cv.y * v.y;
+                        vy += cv.x * v.y + cv.y * v.x;
+                    }
+                    y[m] = make_double2(vx * inv, vy * inv);
+                    ys0[row[m]] = from_d2_mc<T2>(y[m]);
+                    ynew[m] = y[m];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) k[0][m] = rhs_row(row[m], ys0);
+            double n2 = 0.0;
+            norm2_ynew(&n2);  // ynew == y here: |psi|^2 after the jump
+            if (tid == 0) norm2 = n2;
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (status != QTL_OK) atomicCAS((int*)&J.info->status, 0, status);
+        atomicAdd((unsigned long long*)&J.info->steps_acc, (unsigned long long)acc_steps);
+        atomicAdd((unsigned long long*)&J.info->steps_rej, (unsigned long long)rej_steps);
+        atomicAdd((unsigned long long*)&J.info->rhs_evals, (unsigned long long)rhs_evals);
+        atomicAdd((unsigned long long*)&J.info->jumps, (unsigned long long)jumps);
+    }
+}
+
+// Mean over trajectories in a fixed order: one CTA per (e_op, time) pair.
+__global__ void mc_reduce_kernel(const double2* __restrict__ traj_expect, double2* __restrict__ expect,
+                                 int nrows, int ntraj) {
+    __shared__ double sx[32], sy[32];
+    for (int rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+        const double2* src = traj_expect + (size_t)rr * ntraj;
+        double ax = 0.0, ay = 0.0;
+        for (int j = threadIdx.x; j < ntraj; j += blockDim.x) {
+            double2 v = src[j];
+            ax += v.x;
+            ay += v.y;
+        }
+        ax = mc_warp_sum(ax);
+        ay = mc_warp_sum(ay);
+        if ((threadIdx.x & 31) == 0) {
+            sx[threadIdx.x >> 5] = ax;
+            sy[threadIdx.x >> 5] = ay;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tx = 0.0, ty = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                tx += sx[w];
+                ty += sy[w];
+            }
+            expect[rr] = make_double2(tx / ntraj, ty / ntraj);
+        }
+        __syncthreads();
+    }
+}
+
+int mc_traj_capacity() { return MC_TMAX * 4; }
+
+
+// Block sizes with their launch bounds: 4 rows per thread, the smallest
+// block that covers n.
+static int mc_block(int n) {
+    const int sizes[3] = {32, 128, 256};
+    for (int s : sizes)
+        if (4 * s >= n) return s;
+    return 0;
+}
+
+template <bool MIXED, int MAXT>
+static cudaError_t mc_launch_t(const McJob& J, cudaStream_t st) {
+    using T2 = typename MPrec<MIXED>::T2;
+    const int T = MAXT;
+    size_t smem = (size_t)J.n * (sizeof(double2) + 2 * sizeof(T2)) + 16 +
+                  (size_t)(T / 32 + 1) * mc_red_stride(J.n_e, J.n_c) * sizeof(double) + 32;
+    if (J.a_smem) smem += 16 + (size_t)J.n * sizeof(int4) + (size_t)J.a_nnz * (sizeof(T2) + 4);
+    auto kern = mc_traj_kernel<MIXED, 4, MAXT>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int grid = per_sm * nsm;
+    if (grid > J.ntraj) grid = J.ntraj;
+    count_launch();
+    kern<<<grid, T, smem, st>>>(J);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_traj(const McJob& J0, int precision, cudaStream_t st) {
+    const int T = mc_block(J0.n);
+    if (T == 0) return cudaErrorInvalidValue;
+    // Copy A into shared memory when it fits next to the state buffers.
+    McJob J = J0;
+    const size_t tv = precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
+    const size_t base = (size_t)J.n * (sizeof(double2) + 2 * tv) + 64 +
+                        (size_t)(T / 32 + 1) * mc_red_stride(J.n_e, J.n_c) * sizeof(double);
+    J.a_smem = base + 16 + (size_t)J.n * sizeof(int4) + (size_t)J.a_nnz * (tv + 4) <= 200 * 1024;
+    const bool mx = precision == QTL_MIXED;
+    switch (T) {
+        case 32: return mx ? mc_launch_t<true, 32>(J, st) : mc_launch_t<false, 32>(J, st);
+        case 128: return mx ? mc_launch_t<true, 128>(J, st) : mc_launch_t<false, 128>(J, st);
+        default: return mx ? mc_launch_t<true, 256>(J, st) : mc_launch_t<false, 256>(J, st);
+    }
+}
+
+cudaError_t launch_mc_reduce(const McJob& J, cudaStream_t st) {
+    int nrows = J.n_e * J.nt;
+    if (nrows == 0) return cudaSuccess;
+    int grid = nrows < 4096 ? nrows : 4096;
+    count_launch();
+    mc_reduce_kernel<<<grid, 256, 0, st>>>(J.traj_expect, J.expect, nrows, J.ntraj);
+    return cudaGetLastError();
+}
+
+}  // namespace qtl

@@ -1,0 +1,682 @@
+// mesolve on a thread-block cluster: one solve of the Lindblad master
+// equation (paper Sec. 3.2) integrated entirely on the device by one cluster
+// of up to 16 CTAs: adaptive RK 5(4) steps, error norm, PI controller, exact
+// landing on tlist and Tr(O_k rho) inside one launch.
+//
+// Layout.  vec(rho) (column stacking, L = n^2 complex entries) is split over
+// the cluster: CTA c owns rows r = c + C*q, and its thread t holds the rows
+// q = t + 256*m (m < RPT).  The owned rows of y, y_new and k_1..k_7 live in
+// registers.  The stage input y_s = y + h sum_j a_sj k_j of a CTA's rows is
+// written to that CTA's shared memory (two alternating buffers), and the
+// Liouvillian SpMV gathers it from the owning CTAs over distributed shared
+// memory.  Each CTA keeps its rows of the (constant) Liouvillian in shared
+// memory too, every column stored as its DSMEM address.  One cluster barrier
+// per stage and one per step for the error norm.
+//
+// Control.  GB300 runs FP64 at 1/64 of the FP32 rate and a warp-wide FP64
+// instruction holds a sub-partition's FP64 pipe for ~64 cycles, so the scalar
+// control (controller, tlist landing, step bookkeeping) runs in thread 0 of
+// each CTA only, from bitwise identical inputs in every CTA, and is broadcast
+// through shared memory.  The controller's factor is evaluated in FP32 and
+// the error norm's per-entry ratios and their reduction are FP32 (the norm
+// only steers the step size).  y, its update and the expectation values are
+// FP64.
+//
+// Expectation values.  At a landing step every CTA sums w_e(r) * rho_r over
+// its own rows in FP64 and stores the CTA partial; the partials are added in
+// rank order at the end of the solve, so they cost no cluster barrier.
+//
+// Precision.  FP64: Liouvillian, stage sums and SpMV in FP64.  MIXED: those in
+// FP32 (complex64 operator), with y and y_new = y + h sum_j b_j k_j in FP64.
+#include <cooperative_groups.h>
+
+#include "internal.h"
+#include "rk.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace qtl {
+
+constexpr int ME_T = 256;
+constexpr int ME_NW = ME_T / 32;
+constexpr int ME_CMAX = 16;
+constexpr int ME_EMAX = 64;
+
+enum { ACT_STEP = 0, ACT_REPEAT = 1, ACT_DONE = 2 };
+
+template <bool MIXED>
+struct Prec;
+template <>
+struct Prec<false> {
+    using T = double;
+    using T2 = double2;
+};
+template <>
+struct Prec<true> {
+    using T = float;
+    using T2 = float2;
+};
+
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
+template <class T2>
+__device__ __forceinline__ T2 from_d2(double2 v);
+template <>
+__device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <>
+__device__ __forceinline__ float2 from_d2<float2>(double2 v) {
+    return make_float2((float)v.x, (float)v.y);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t dsmem_map(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ double2 ld_dsmem(uint32_t a, double2*) {
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 ld_dsmem(uint32_t a, float2*) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float ld_dsmem_f(uint32_t a) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+
+template <class V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct MeShared {
+    float wf[ME_NW];               // warp partials of the error / start-step sums
+    float wf2[ME_NW];
+    float pf[2][2];                // CTA partials, double-buffered across reductions
+    double we[ME_NW][2 * ME_EMAX]; // warp partials of the expectation values
+    double coef[28];               // htry * a_sj (21, packed by stage) and htry * e_j (7)
+    double h0, d1;
+    int action, land, accept, save_idx, repeat_idx;
+    int scan[ME_NW];
+};
+
+// Row q of this CTA's cached Liouvillian times the stage input held in the
+// cluster's shared memory (buffer offset bufoff): real-only entries,
+// imaginary-only entries, then complex entries.
+template <class T2, class TV>
+__device__ __forceinline__ T2 spmv_dsm(int q, const int4* __restrict__ s_seg,
+                                       const uint32_t* __restrict__ s_addr,
+                                       const TV* __restrict__ s_v, uint32_t bufoff) {
+    const int4 sg = s_seg[q];
+    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
+    int p = sg.x;
+#pragma unroll 4
+    for (; p < sg.y; ++p) {
+        const decltype(T2::x) v = s_v[p].x;
+        const T2 xv = ld_dsmem(s_addr[p] + bufoff, (T2*)nullptr);
+        ax = fma(v, xv.x, ax);
+        ay = fma(v, xv.y, ay);
+    }
+#pragma unroll 4
+    for (; p < sg.z; ++p) {
+        const decltype(T2::x) v = s_v[p].y;
+        const T2 xv = ld_dsmem(s_addr[p] + bufoff, (T2*)nullptr);
+        bx = fma(-v, xv.y, bx);
+        by = fma(v, xv.x, by);
+    }
+#pragma unroll 2
+    for (; p < sg.w; ++p) {
+        const TV v = s_v[p];
+        const T2 xv = ld_dsmem(s_addr[p] + bufoff, (T2*)nullptr);
+        ax = fma(v.x, xv.x, ax);
+        ay = fma(v.x, xv.y, ay);
+        bx = fma(-v.y, xv.y, bx);
+        by = fma(v.y, xv.x, by);
+    }
+    T2 acc;
+    acc.x = ax + bx;
+    acc.y = ay + by;
+    return acc;
+}
+
+// Exclusive prefix sum of v over the CTA; *total gets the sum.
+__device__ __forceinline__ int cta_exclusive_scan(int v, int* scratch, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) scratch[warp] = x;
+    __syncthreads();
+    int base = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < ME_NW; ++w) {
+        if (w < warp) base += scratch[w];
+        tot += scratch[w];
+    }
+    __syncthreads();
+    *total = tot;
+    return base + x - v;
+}
+
+// Index of h*a_sj in MeShared::coef (stages s = 1..6, j < s).
+__host__ __device__ constexpr int coef_a(int s, int j) { return s * (s - 1) / 2 + j; }
+
+template <bool MIXED, int RPT>
+__device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, unsigned char* dsm) {
+    using T = typename Prec<MIXED>::T;
+    using T2 = typename Prec<MIXED>::T2;
+    using TV = T2;
+    const int C = (int)cl.num_blocks();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rank = (int)cl.block_rank();
+    const int L = J.L, n = J.n, NE2 = 2 * J.n_e;
+    const RkTab& tab = RK_TABS[J.method];
+    const TV* lv = MIXED ? (const TV*)J.lv32 : (const TV*)J.lv64;
+
+    // dynamic shared memory: ys[2][RPT*256], seg[RPT*256], addr[cap], v[cap]
+    T2* s_ys = (T2*)dsm;
+    const uint32_t bufoff = (uint32_t)(RPT * ME_T * sizeof(T2));
+    int4* s_seg = (int4*)(s_ys + 2 * RPT * ME_T);
+    uint32_t* s_addr = (uint32_t*)(s_seg + RPT * ME_T);
+    TV* s_v = (TV*)(((uintptr_t)(s_addr + J.smem_nnz) + 15) & ~(uintptr_t)15);
+    const uint32_t ys_base = smem_addr(s_ys);
+
+    double2 y[RPT], ynew[RPT];
+    T2 k[7][RPT];
+    bool own[RPT];
+    int row[RPT];
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+        row[m] = rank + C * (tid + ME_T * m);
+        own[m] = row[m] < L;
+        y[m] = make_double2(0.0, 0.0);
+        if (own[m]) {
+            if (J.is_ket) {  // rho0 = |psi0><psi0| (ket2dm)
+                const int i = row[m] % n, j = row[m] / n;
+                const double2 a = J.state0[i], b = J.state0[j];
+                y[m] = make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+            } else {
+                y[m] = J.state0[row[m]];
+            }
+        }
+        ynew[m] = y[m];
+        s_ys[tid + ME_T * m] = from_d2<T2>(y[m]);
+    }
+
+    // ---- this CTA's rows of the Liouvillian into shared memory ----
+    {
+        int cnt = 0;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m)
+            if (own[m]) {
+                const int4 sg = __ldg(J.seg + row[m]);
+                cnt += sg.w - sg.x;
+            }
+        int total = 0;
+        int off = cta_exclusive_scan(cnt, sh.scan, &total);
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            const int q = tid + ME_T * m;
+            if (!own[m]) {
+                s_seg[q] = make_int4(0, 0, 0, 0);
+                continue;
+            }
+            const int4 sg = __ldg(J.seg + row[m]);
+            for (int p = sg.x; p < sg.w; ++p) {
+                const int c = __ldg(J.ci + p);
+                s_addr[off + p - sg.x] =
+                    dsmem_map(ys_base + (uint32_t)((c / C) * sizeof(T2)), (uint32_t)(c % C));
+                s_v[off + p - sg.x] = __ldg(lv + p);
+            }
+            s_seg[q] = make_int4(off, off + sg.y - sg.x, off + sg.z - sg.x, off + sg.w - sg.x);
+            off += sg.w - sg.x;
+        }
+    }
+    cl.sync();
+
+    // Per-CTA FP64 partials of Tr(O_e rho) over own rows -> J.epart[idx][rank][*].
+    auto expect_partials = [&](const double2* v, int idx) {
+        for (int e = 0; e < J.n_e; ++e) {
+            double sr = 0.0, si = 0.0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (!own[m]) continue;
+                const double2 w = __ldg(J.ew + (size_t)row[m] * J.n_e + e);
+                sr += w.x * v[m].x - w.y * v[m].y;
+                si += w.x * v[m].y + w.y * v[m].x;
+            }
+            sr = warp_sum(sr);
+            si = warp_sum(si);
+            if (lane == 0) {
+                sh.we[warp][2 * e] = sr;
+                sh.we[warp][2 * e + 1] = si;
+            }
+        }
+        __syncthreads();
+        if (tid < NE2) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < ME_NW; ++w) s += sh.we[w][tid];
+            J.epart[((size_t)idx * C + rank) * NE2 + tid] = s;
+        }
+    };
+    auto states_write = [&](int idx) {
+        if (J.states) {
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) J.states[(size_t)idx * L + row[m]] = y[m];
+        }
+    };
+    // Cluster-wide FP32 sums of (a, b): warp -> CTA (thread 0) -> cluster
+    // (thread 0 of every CTA reads all CTAs' partials in rank order).
+    int par = 0;
+    auto reduce2 = [&](float a, float b, float* out_a, float* out_b) {
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (lane == 0) {
+            sh.wf[warp] = a;
+            sh.wf2[warp] = b;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int w = 0; w < ME_NW; ++w) {
+                sa += sh.wf[w];
+                sb += sh.wf2[w];
+            }
+            sh.pf[par][0] = sa;
+            sh.pf[par][1] = sb;
+        }
+        cl.sync();
+        if (tid == 0) {
+            const uint32_t base = smem_addr(&sh.pf[par][0]);
+            float va[ME_CMAX], vb[ME_CMAX];
+#pragma unroll
+            for (int r = 0; r < ME_CMAX; ++r) {
+                if (r < C) {
+                    const uint32_t a_r = dsmem_map(base, (uint32_t)r);
+                    va[r] = ld_dsmem_f(a_r);
+                    vb[r] = ld_dsmem_f(a_r + 4);
+                } else {
+                    va[r] = 0.f;
+                    vb[r] = 0.f;
+                }
+            }
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int r = 0; r < ME_CMAX; ++r) {
+                sa += va[r];
+                sb += vb[r];
+            }
+            *out_a = sa;
+            *out_b = sb;
+        }
+        par ^= 1;
+    };
+
+    // k1 = L y0, expectation values at tlist[0]
+#pragma unroll
+    for (int m = 0; m < RPT; ++m)
+        if (own[m]) k[0][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, 0u);
+    expect_partials(y, 0);
+    states_write(0);
+
+    // thread-0 control state (identical in every CTA)
+    double t = J.tlist[0], h = 0.0, htry = 0.0, t_target = 0.0;
+    int idx = 1, status = QTL_OK;
+    long long attempts = 0, steps_acc = 0, steps_rej = 0, rhs_evals = 1;
+    CtlF ctl;
+    ctl.init();
+
+    // ---- starting step ----
+    if (J.fixed) {
+        h = J.dt_fixed;
+    } else if (J.dt0 > 0.0) {
+        h = J.dt0;
+    } else {
+        // Hairer-Norsett-Wanner: d0 = |y0|, d1 = |f0| (RMS, scaled by
+        // atol + rtol |y0|), h0 = 0.01 d0/d1, d2 = |f(y0 + h0 f0) - f0| / h0.
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            if (!own[m]) continue;
+            const double2 f0 = to_d2(k[0][m]);
+            const float a = sqrtf((float)(y[m].x * y[m].x + y[m].y * y[m].y));
+            const float sc = (float)J.atol + (float)J.rtol * a;
+            const float q0 = a / sc;
+            const float q1 = sqrtf((float)(f0.x * f0.x + f0.y * f0.y)) / sc;
+            s0 += q0 * q0;
+            s1 += q1 * q1;
+        }
+        float S0 = 0.f, S1 = 0.f;
+        reduce2(s0, s1, &S0, &S1);
+        if (tid == 0) {
+            const double d0 = sqrt((double)S0 / L), d1 = sqrt((double)S1 / L);
+            sh.h0 = start_h0(d0, d1);
+            sh.d1 = d1;
+        }
+        __syncthreads();
+        const double h0 = sh.h0;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            const double2 f0 = to_d2(k[0][m]);
+            s_ys[RPT * ME_T + tid + ME_T * m] =
+                from_d2<T2>(make_double2(y[m].x + h0 * f0.x, y[m].y + h0 * f0.y));
+        }
+        cl.sync();
+        float s2 = 0.f;
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            if (!own[m]) continue;
+            const double2 f1 = to_d2(spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff));
+            const double2 f0 = to_d2(k[0][m]);
+            const float a = sqrtf((float)(y[m].x * y[m].x + y[m].y * y[m].y));
+            const float sc = (float)J.atol + (float)J.rtol * a;
+            const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
+            const float q = sqrtf(dx * dx + dy * dy) / sc;
+            s2 += q * q;
+        }
+        float S2 = 0.f, dummy = 0.f;
+        reduce2(s2, 0.f, &S2, &dummy);
+        if (tid == 0) {
+            rhs_evals += 1;
+            h = start_h(h0, sh.d1, sqrt((double)S2 / L) / h0);
+        }
+    }
+    // every CTA has finished gathering from buffers 0/1 before they are rewritten
+    cl.sync();
+
+    // thread 0: choose the next action (step / repeated output time / done)
+    auto next_action = [&]() {
+        for (;;) {
+            if (status != QTL_OK || idx >= J.nt) {
+                sh.action = ACT_DONE;
+                return;
+            }
+            t_target = J.tlist[idx];
+            if (!(t_target >= J.tlist[idx - 1]) || !isfinite(t_target)) {
+                status = QTL_EINVAL;
+                continue;
+            }
+            if (!(t < t_target)) {
+                sh.action = ACT_REPEAT;
+                sh.repeat_idx = idx++;
+                return;
+            }
+            if (attempts >= J.max_steps) {
+                status = QTL_ESTEP;
+                continue;
+            }
+            ++attempts;
+            const bool land = lands(h, t, t_target);
+            htry = land ? (t_target - t) : h;
+            sh.land = land;
+            sh.action = ACT_STEP;
+            sh.coef[27] = htry;  // handed to warp 0 for the coefficient products
+            return;
+        }
+    };
+    // warp 0: the 28 products htry * (a_sj, e_j) in FP64, one per lane
+    auto publish_coefs = [&]() {
+        __syncwarp();
+        if (sh.action == ACT_STEP) {
+            const double hh = sh.coef[27];
+            __syncwarp();
+            if (lane < 21) {
+                int s = 1, j = lane;
+                while (j >= s) {
+                    j -= s;
+                    ++s;
+                }
+                sh.coef[lane] = hh * tab.a[s][j];
+            } else if (lane < 28) {
+                sh.coef[lane] = hh * tab.e[lane - 21];
+            }
+        }
+    };
+    if (tid == 0) next_action();
+    if (warp == 0) publish_coefs();
+    __syncthreads();
+
+    // ---- main loop: one iteration per step attempt ----
+    for (;;) {
+        const int action = sh.action;
+        if (action == ACT_DONE) break;
+        if (action == ACT_REPEAT) {
+            const int ri = sh.repeat_idx;
+            if (tid < NE2)
+                J.epart[((size_t)ri * C + rank) * NE2 + tid] =
+                    __ldcg(J.epart + ((size_t)(ri - 1) * C + rank) * NE2 + tid);
+            states_write(ri);
+            __syncthreads();
+            if (tid == 0) next_action();
+            if (warp == 0) publish_coefs();
+            __syncthreads();
+            continue;
+        }
+        const bool land = sh.land;
+        // stages 2..7: combine own rows -> own shared memory -> barrier -> SpMV
+#pragma unroll
+        for (int s = 1; s < 7; ++s) {
+            const uint32_t off = (s & 1) ? 0u : bufoff;
+            T2* ysb = s_ys + ((s & 1) ? 0 : RPT * ME_T);
+            T ha[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) ha[j] = j < s ? (T)sh.coef[coef_a(s, j)] : (T)0;
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                T ax = 0, ay = 0;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    if (j < s) {
+                        ax = fma(ha[j], k[j][m].x, ax);
+                        ay = fma(ha[j], k[j][m].y, ay);
+                    }
+                }
+                T2 o;
+                if (s == 6) {
+                    ynew[m] = make_double2(y[m].x + (double)ax, y[m].y + (double)ay);
+                    o = from_d2<T2>(ynew[m]);
+                } else {
+                    o.x = (T)y[m].x + ax;
+                    o.y = (T)y[m].y + ay;
+                }
+                ysb[tid + ME_T * m] = o;
+            }
+            cl.sync();
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+        }
+        // error norm: sum over own rows of (|e| / sc)^2, e = h sum_j e_j k_j
+        float se = 0.f;
+        {
+            T he[7];
+#pragma unroll
+            for (int j = 0; j < 7; ++j) he[j] = (T)sh.coef[21 + j];
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (!own[m]) continue;
+                T ex = 0, ey = 0;
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    ex = fma(he[j], k[j][m].x, ex);
+                    ey = fma(he[j], k[j][m].y, ey);
+                }
+                const float yx = (float)y[m].x, yy = (float)y[m].y;
+                const float nx = (float)ynew[m].x, ny = (float)ynew[m].y;
+                const float a2 = fmaxf(yx * yx + yy * yy, nx * nx + ny * ny);
+                const float sc = (float)J.atol + (float)J.rtol * sqrtf(a2);
+                const float fx = (float)ex, fy = (float)ey;
+                se += (fx * fx + fy * fy) / (sc * sc);
+            }
+        }
+        if (land) {
+            // expectation values of the candidate state (kept only if accepted)
+            if (tid == 0) sh.save_idx = idx;
+            __syncthreads();
+            expect_partials(ynew, sh.save_idx);
+        }
+        float S = 0.f, dummy = 0.f;
+        reduce2(se, 0.f, &S, &dummy);
+        // ---- decision (thread 0), then the next action ----
+        if (tid == 0) {
+            rhs_evals += 6;
+            const float err = sqrtf(S / (float)L);
+            bool acc = true;
+            float fac = 1.0f;
+            if (!J.fixed) {
+                if (!(S <= (float)L)) {
+                    acc = false;
+                    ++steps_rej;
+                    h = htry * (double)ctl.on_reject(err);
+                    if (h < J.dt_min || !isfinite(S)) status = QTL_ESTEP;
+                } else {
+                    fac = ctl.on_accept(err);
+                }
+            }
+            sh.accept = acc;
+            if (acc) {
+                ++steps_acc;
+                t = land ? t_target : t + htry;
+                h = J.fixed ? J.dt_fixed : htry * (double)fac;
+                if (land) ++idx;
+            }
+            next_action();
+        }
+        if (warp == 0) publish_coefs();
+        __syncthreads();
+        if (sh.accept) {
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                y[m] = ynew[m];
+                k[0][m] = k[6][m];
+            }
+            if (land) states_write(sh.save_idx);
+        }
+    }
+
+    // ---- expectation values: CTA partials added in rank order ----
+    cl.sync();
+    if (rank == 0) {
+        for (int v = tid; v < J.nt * NE2; v += ME_T) {
+            const int ti = v / NE2, c2 = v % NE2;
+            double s = 0.0;
+            for (int r = 0; r < C; ++r) s += __ldcg(J.epart + ((size_t)ti * C + r) * NE2 + c2);
+            double* ex = (double*)(J.expect + (size_t)(c2 >> 1) * J.nt + ti);
+            ex[c2 & 1] = s;
+        }
+        if (tid == 0) {
+            J.info->status = status;
+            J.info->steps_acc = steps_acc;
+            J.info->steps_rej = steps_rej;
+            J.info->rhs_evals = rhs_evals;
+            J.info->jumps = 0;
+        }
+    }
+}
+
+template <bool MIXED, int RPT>
+__global__ void __launch_bounds__(ME_T, 1) me_cluster_kernel(const MeJob* __restrict__ jobs,
+                                                              int njobs) {
+    __shared__ MeShared sh;
+    extern __shared__ __align__(16) unsigned char me_dsm[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int cid = blockIdx.x / C, ncl = gridDim.x / C;
+    for (int jb = cid; jb < njobs; jb += ncl) {
+        const MeJob J = jobs[jb];
+        me_solve<MIXED, RPT>(J, sh, cl, me_dsm);
+        cl.sync();
+    }
+}
+
+int me_cluster_capacity() { return ME_CMAX * ME_T * 4; }
+
+bool me_plan(int L_max, int cluster_size, int* C_out, int* rpt_out) {
+    // Default: 16 CTAs (one per SM), the most SMs a cluster can bring to one
+    // solve; rows per thread the smallest of 1, 2, 4 that covers L.
+    int C = cluster_size > 0 ? cluster_size : ME_CMAX;
+    int rpt = 1;
+    while (rpt < 4 && (long long)C * ME_T * rpt < L_max) rpt *= 2;
+    *C_out = C;
+    *rpt_out = rpt;
+    return C <= ME_CMAX && (long long)C * ME_T * rpt >= L_max;
+}
+
+static size_t me_dyn_smem(int precision, int rpt, int nnz) {
+    const size_t t2 = precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
+    return 2 * (size_t)rpt * ME_T * t2 + (size_t)rpt * ME_T * sizeof(int4) + (size_t)nnz * 4 + 16 +
+           (size_t)nnz * t2;
+}
+
+int me_smem_nnz_budget(int precision, int rpt) {
+    const size_t limit = 200 * 1024;
+    const size_t t2 = precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
+    const size_t fixed = me_dyn_smem(precision, rpt, 0);
+    return fixed >= limit ? 0 : (int)((limit - fixed) / (4 + t2));
+}
+
+template <bool MIXED, int RPT>
+static cudaError_t launch_t(const MeJob* jobs, int njobs, int C, int nclusters, int smem_nnz,
+                            cudaStream_t st) {
+    auto kern = me_cluster_kernel<MIXED, RPT>;
+    const size_t dsm = me_dyn_smem(MIXED ? QTL_MIXED : QTL_FP64, RPT, smem_nnz);
+    cudaError_t e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C * nclusters);
+    cfg.blockDim = dim3(ME_T);
+    cfg.dynamicSmemBytes = dsm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, kern, jobs, njobs);
+}
+
+cudaError_t launch_me_cluster(const MeJob* jobs_dev, int njobs, int L_max, int smem_nnz,
+                              int precision, int cluster_size, cudaStream_t st) {
+    int C, rpt;
+    if (!me_plan(L_max, cluster_size, &C, &rpt)) return cudaErrorInvalidValue;
+    if (smem_nnz > me_smem_nnz_budget(precision, rpt)) return cudaErrorInvalidValue;
+    int nclusters = njobs;
+    const int cap = (2 * 152) / C > 0 ? (2 * 152) / C : 1;
+    if (nclusters > cap) nclusters = cap;
+    if (nclusters < 1) nclusters = 1;
+    const bool mixed = precision == QTL_MIXED;
+    if (mixed) {
+        if (rpt == 1) return launch_t<true, 1>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+        if (rpt == 2) return launch_t<true, 2>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+        return launch_t<true, 4>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+    }
+    if (rpt == 1) return launch_t<false, 1>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+    if (rpt == 2) return launch_t<false, 2>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+    return launch_t<false, 4>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+}
+
+}  // namespace qtl

@@ -1,0 +1,639 @@
+// Host runtime behind the C ABI (include/qtl.h): operator validation and
+// conversion to CSR, the FP64 host build of A = -i H - 1/2 sum C^dag C,
+// B^T and the column-stacking Liouvillian (paper Sec. 3.2 / 3.3), device
+// uploads, and the mesolve / mcsolve drivers that enqueue the kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace qtl {
+
+using cplx = std::complex<double>;
+
+static std::atomic<long long> g_launches{0};
+static thread_local std::string g_cuda_err;
+
+void count_launch(int k) { g_launches += k; }
+void set_cuda_error(cudaError_t e) {
+    g_cuda_err = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
+}
+
+#define QTL_CUDA(call)                         \
+    do {                                       \
+        cudaError_t e_ = (call);               \
+        if (e_ != cudaSuccess) {               \
+            set_cuda_error(e_);                \
+            return e_ == cudaErrorMemoryAllocation ? QTL_ENOMEM : QTL_ECUDA; \
+        }                                      \
+    } while (0)
+
+// ------------------------------------------------------------ CSR helpers
+static bool finite_c(const qtl_c128& v) { return std::isfinite(v.re) && std::isfinite(v.im); }
+
+// Converts a qtl_op to a canonical CSR: columns sorted, duplicates summed,
+// exact zeros dropped.
+static qtl_status to_csr(const qtl_op* op, int n_expect, Csr& out) {
+    if (!op || op->n <= 0 || op->n > 46340 || (n_expect > 0 && op->n != n_expect)) return QTL_EINVAL;
+    if (!op->vals) return QTL_EINVAL;
+    const int n = op->n;
+    out = Csr();
+    out.n = n;
+    out.rp.assign(n + 1, 0);
+    std::vector<std::pair<int32_t, cplx>> rowbuf;
+    if (op->is_csr) {
+        if (!op->row_ptr || (op->nnz > 0 && !op->col_idx) || op->nnz < 0) return QTL_EINVAL;
+        if (op->row_ptr[0] != 0 || op->row_ptr[n] != op->nnz) return QTL_EINVAL;
+        for (int i = 0; i < n; ++i)
+            if (op->row_ptr[i + 1] < op->row_ptr[i]) return QTL_EINVAL;
+        for (int i = 0; i < n; ++i) {
+            rowbuf.clear();
+            for (int64_t p = op->row_ptr[i]; p < op->row_ptr[i + 1]; ++p) {
+                int32_t c = op->col_idx[p];
+                if (c < 0 || c >= n || !finite_c(op->vals[p])) return QTL_EINVAL;
+                rowbuf.emplace_back(c, cplx(op->vals[p].re, op->vals[p].im));
+            }
+            std::sort(rowbuf.begin(), rowbuf.end(),
+                      [](const auto& a, const auto& b) { return a.first < b.first; });
+            for (size_t q = 0; q < rowbuf.size();) {
+                int32_t c = rowbuf[q].first;
+                cplx s = 0;
+                while (q < rowbuf.size() && rowbuf[q].first == c) s += rowbuf[q++].second;
+                if (s != cplx(0)) {
+                    out.ci.push_back(c);
+                    out.re.push_back(s.real());
+                    out.im.push_back(s.imag());
+                }
+            }
+            out.rp[i + 1] = (int32_t)out.ci.size();
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                const qtl_c128& v = op->vals[(size_t)j * n + i];
+                if (!finite_c(v)) return QTL_EINVAL;
+                if (v.re != 0.0 || v.im != 0.0) {
+                    out.ci.push_back(j);
+                    out.re.push_back(v.re);
+                    out.im.push_back(v.im);
+                }
+            }
+            out.rp[i + 1] = (int32_t)out.ci.size();
+        }
+    }
+    return QTL_OK;
+}
+
+static cplx at(const Csr& m, int64_t p) { return cplx(m.re[p], m.im[p]); }
+
+// Builds a CSR from per-row (col, value) lists.
+static void rows_to_csr(int n, std::vector<std::vector<std::pair<int32_t, cplx>>>& rows, Csr& out) {
+    out = Csr();
+    out.n = n;
+    out.rp.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        auto& r = rows[i];
+        std::sort(r.begin(), r.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+        for (size_t q = 0; q < r.size();) {
+            int32_t c = r[q].first;
+            cplx s = 0;
+            while (q < r.size() && r[q].first == c) s += r[q++].second;
+            if (s != cplx(0)) {
+                out.ci.push_back(c);
+                out.re.push_back(s.real());
+                out.im.push_back(s.imag());
+            }
+        }
+        out.rp[i + 1] = (int32_t)out.ci.size();
+        r.clear();
+        r.shrink_to_fit();
+    }
+}
+
+// G = sum_k C_k^dag C_k:  G_ij = sum_k sum_l conj(C_k[l,i]) C_k[l,j].
+static void sum_cdagc(int n, const std::vector<Csr>& C, Csr& G) {
+    std::vector<std::vector<std::pair<int32_t, cplx>>> rows(n);
+    for (const Csr& c : C)
+        for (int l = 0; l < n; ++l)
+            for (int64_t p = c.rp[l]; p < c.rp[l + 1]; ++p)
+                for (int64_t q = c.rp[l]; q < c.rp[l + 1]; ++q)
+                    rows[c.ci[p]].emplace_back(c.ci[q], std::conj(at(c, p)) * at(c, q));
+    rows_to_csr(n, rows, G);
+}
+
+// A = -i H - G/2 and B^T with B = i H - G/2 (rows of B^T are columns of B).
+static void build_a_bt(const Csr& H, const Csr& G, Csr& A, Csr& Bt) {
+    const int n = H.n;
+    std::vector<std::vector<std::pair<int32_t, cplx>>> ra(n), rb(n);
+    const cplx I(0, 1);
+    for (int i = 0; i < n; ++i) {
+        for (int64_t p = H.rp[i]; p < H.rp[i + 1]; ++p) {
+            ra[i].emplace_back(H.ci[p], -I * at(H, p));
+            rb[H.ci[p]].emplace_back(i, I * at(H, p));
+        }
+        for (int64_t p = G.rp[i]; p < G.rp[i + 1]; ++p) {
+            ra[i].emplace_back(G.ci[p], -0.5 * at(G, p));
+            rb[G.ci[p]].emplace_back(i, -0.5 * at(G, p));
+        }
+    }
+    rows_to_csr(n, ra, A);
+    rows_to_csr(n, rb, Bt);
+}
+
+// Liouvillian for column stacking, row r = i + n j (the entry rho_ij):
+//   (I kron A)        -> A_ik          at column k + n j
+//   (B^T kron I)      -> (B^T)_jl      at column i + n l
+//   (conj(C) kron C)  -> C_ik conj(C_jl) at column k + n l
+static void build_liouvillian(const System& s, Csr& L) {
+    const int n = s.n;
+    const int64_t NL = (int64_t)n * n;
+    L = Csr();
+    L.n = (int)NL;
+    L.rp.assign(NL + 1, 0);
+    std::vector<std::pair<int32_t, cplx>> row;
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < n; ++i) {
+            row.clear();
+            for (int64_t p = s.A.rp[i]; p < s.A.rp[i + 1]; ++p)
+                row.emplace_back(s.A.ci[p] + n * j, at(s.A, p));
+            for (int64_t p = s.Bt.rp[j]; p < s.Bt.rp[j + 1]; ++p)
+                row.emplace_back(i + n * s.Bt.ci[p], at(s.Bt, p));
+            for (const Csr& c : s.C)
+                for (int64_t p = c.rp[i]; p < c.rp[i + 1]; ++p)
+                    for (int64_t q = c.rp[j]; q < c.rp[j + 1]; ++q)
+                        row.emplace_back(c.ci[p] + n * c.ci[q], at(c, p) * std::conj(at(c, q)));
+            std::sort(row.begin(), row.end(),
+                      [](const auto& a, const auto& b) { return a.first < b.first; });
+            for (size_t q = 0; q < row.size();) {
+                int32_t col = row[q].first;
+                cplx v = 0;
+                while (q < row.size() && row[q].first == col) v += row[q++].second;
+                if (v != cplx(0)) {
+                    L.ci.push_back(col);
+                    L.re.push_back(v.real());
+                    L.im.push_back(v.imag());
+                }
+            }
+            L.rp[(int64_t)i + (int64_t)n * j + 1] = (int32_t)L.ci.size();
+        }
+    }
+}
+
+// Stacks operators row-wise (operator k occupies rows k*n .. k*n+n-1).
+static void stack(const std::vector<Csr>& ops, int n, Csr& out) {
+    out = Csr();
+    out.n = n * (int)ops.size();
+    out.rp.assign((size_t)out.n + 1, 0);
+    int r = 0;
+    for (const Csr& o : ops) {
+        for (int i = 0; i < n; ++i, ++r) {
+            for (int64_t p = o.rp[i]; p < o.rp[i + 1]; ++p) {
+                out.ci.push_back(o.ci[p]);
+                out.re.push_back(o.re[p]);
+                out.im.push_back(o.im[p]);
+            }
+            out.rp[r + 1] = (int32_t)out.ci.size();
+        }
+    }
+}
+
+template <class T>
+static qtl_status upload(T** dst, const T* src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) return QTL_OK;
+    QTL_CUDA(cudaMalloc((void**)dst, count * sizeof(T)));
+    QTL_CUDA(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice));
+    return QTL_OK;
+}
+
+static qtl_status upload_csr(const Csr& m, DevCsr& d) {
+    d.n = m.n;
+    d.nnz = m.nnz();
+    std::vector<double2> v64(m.nnz());
+    std::vector<float2> v32(m.nnz());
+    std::vector<int32_t> ci(m.nnz());
+    std::vector<int4> seg(m.n);
+    for (int r = 0; r < m.n; ++r) {
+        // group the row's entries: real-only, imaginary-only, complex
+        int32_t q = m.rp[r];
+        int b[3];
+        for (int grp = 0; grp < 3; ++grp) {
+            b[grp] = q;
+            for (int64_t p = m.rp[r]; p < m.rp[r + 1]; ++p) {
+                const bool re0 = m.re[p] == 0.0, im0 = m.im[p] == 0.0;
+                const int gp = im0 ? 0 : (re0 ? 1 : 2);
+                if (gp != grp) continue;
+                ci[q] = m.ci[p];
+                v64[q] = make_double2(m.re[p], m.im[p]);
+                v32[q] = make_float2((float)m.re[p], (float)m.im[p]);
+                ++q;
+            }
+        }
+        seg[r] = make_int4(b[0], b[1], b[2], m.rp[r + 1]);
+    }
+    qtl_status st;
+    if ((st = upload(&d.seg, seg.data(), seg.size())) != QTL_OK) return st;
+    if ((st = upload(&d.rp, m.rp.data(), m.rp.size())) != QTL_OK) return st;
+    if ((st = upload(&d.ci, ci.data(), ci.size())) != QTL_OK) return st;
+    if ((st = upload(&d.v64, v64.data(), v64.size())) != QTL_OK) return st;
+    if ((st = upload(&d.v32, v32.data(), v32.size())) != QTL_OK) return st;
+    return QTL_OK;
+}
+
+static void free_csr(DevCsr& d) {
+    cudaFree(d.seg);
+    cudaFree(d.rp);
+    cudaFree(d.ci);
+    cudaFree(d.v64);
+    cudaFree(d.v32);
+    d = DevCsr();
+}
+
+static std::mutex g_build_mu;
+
+static qtl_status ensure_liouvillian(System& s) {
+    std::lock_guard<std::mutex> lk(g_build_mu);
+    if (s.dL.rp) return QTL_OK;
+    if ((int64_t)s.n * s.n > me_cluster_capacity()) return QTL_ETOOBIG;
+    Csr L;
+    build_liouvillian(s, L);
+    if (L.nnz() >= (int64_t)INT32_MAX) return QTL_ETOOBIG;
+    s.L_rp = L.rp;
+    // Tr(O_e rho) = sum_{i,k} O_ik rho_ki: weight O_ik at vec row k + n i.
+    const size_t NL = (size_t)s.n * s.n;
+    if (s.n_e > 0) {
+        std::vector<double2> ew(NL * s.n_e, make_double2(0.0, 0.0));
+        for (int e = 0; e < s.n_e; ++e) {
+            const Csr& o = s.O[e];
+            for (int i = 0; i < s.n; ++i)
+                for (int64_t p = o.rp[i]; p < o.rp[i + 1]; ++p)
+                    ew[((size_t)o.ci[p] + (size_t)s.n * i) * s.n_e + e] = make_double2(o.re[p], o.im[p]);
+        }
+        qtl_status st = upload(&s.ew, ew.data(), ew.size());
+        if (st != QTL_OK) return st;
+    }
+    return upload_csr(L, s.dL);
+}
+
+static qtl_status check_opts(const qtl_opts* o) {
+    if (!o) return QTL_EINVAL;
+    if (o->method != QTL_DP5 && o->method != QTL_TSIT5) return QTL_EINVAL;
+    if (o->precision != QTL_FP64 && o->precision != QTL_MIXED) return QTL_EINVAL;
+    if (o->fixed_step) {
+        if (!(o->dt_fixed > 0.0) || !std::isfinite(o->dt_fixed)) return QTL_EINVAL;
+    } else {
+        if (!(o->rtol > 0.0) || !(o->atol >= 0.0) || !std::isfinite(o->rtol) || !std::isfinite(o->atol))
+            return QTL_EINVAL;
+    }
+    if (!(o->dt0 >= 0.0) || !(o->dt_min >= 0.0) || o->max_steps <= 0) return QTL_EINVAL;
+    if (o->cluster_size < 0 || o->cluster_size > 16) return QTL_EINVAL;
+    return QTL_OK;
+}
+
+static qtl_status check_tlist_host(const double* tl, int nt) {
+    if (!tl || nt < 1) return QTL_EINVAL;
+    for (int i = 0; i < nt; ++i) {
+        if (!std::isfinite(tl[i])) return QTL_EINVAL;
+        if (i > 0 && tl[i] < tl[i - 1]) return QTL_EINVAL;
+    }
+    return QTL_OK;
+}
+
+}  // namespace qtl
+
+using namespace qtl;
+
+extern "C" {
+
+void qtl_opts_default(qtl_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->method = QTL_TSIT5;
+    o->precision = QTL_FP64;
+    o->rtol = 1e-8;
+    o->atol = 1e-10;
+    o->dt0 = 0.0;
+    o->dt_min = 0.0;
+    o->max_steps = 10000000;
+    o->fixed_step = 0;
+    o->cluster_size = 0;
+    o->dt_fixed = 0.0;
+    o->cuda_stream = nullptr;
+}
+
+const char* qtl_strerror(qtl_status s) {
+    switch (s) {
+        case QTL_OK: return "ok";
+        case QTL_EINVAL: return "invalid argument";
+        case QTL_ENOMEM: return "out of device memory";
+        case QTL_ESTEP: return "step size underflow, max_steps reached or non-finite error";
+        case QTL_ECUDA: return "CUDA error";
+        case QTL_ECANCEL: return "cancelled";
+        case QTL_EBUSY: return "busy";
+        case QTL_ETOOBIG: return "problem too large for the selected kernel";
+    }
+    return "unknown status";
+}
+
+const char* qtl_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int64_t qtl_launch_count(void) { return g_launches.load(); }
+
+void qtl_system_free(qtl_system* sys) {
+    if (!sys) return;
+    System& s = sys->s;
+    free_csr(s.dA);
+    free_csr(s.dC);
+    free_csr(s.dO);
+    free_csr(s.dL);
+    cudaFree(s.ew);
+    delete sys;
+}
+
+qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c, const qtl_op* e_ops,
+                             int32_t n_e, qtl_system** out) {
+    if (!out) return QTL_EINVAL;
+    *out = nullptr;
+    if (!H || n_c < 0 || n_e < 0 || n_c > 64 || n_e > 64) return QTL_EINVAL;
+    if ((n_c > 0 && !c_ops) || (n_e > 0 && !e_ops)) return QTL_EINVAL;
+    qtl_system* sys = new qtl_system();
+    System& s = sys->s;
+    qtl_status st = to_csr(H, 0, s.H);
+    if (st != QTL_OK) {
+        delete sys;
+        return st;
+    }
+    s.n = s.H.n;
+    s.n_c = n_c;
+    s.n_e = n_e;
+    s.C.resize(n_c);
+    s.O.resize(n_e);
+    for (int k = 0; k < n_c && st == QTL_OK; ++k) st = to_csr(&c_ops[k], s.n, s.C[k]);
+    for (int k = 0; k < n_e && st == QTL_OK; ++k) st = to_csr(&e_ops[k], s.n, s.O[k]);
+    if (st != QTL_OK) {
+        delete sys;
+        return st;
+    }
+    cudaGetDevice(&s.device);
+    Csr G;
+    sum_cdagc(s.n, s.C, G);
+    build_a_bt(s.H, G, s.A, s.Bt);
+    Csr Cs, Os;
+    stack(s.C, s.n, Cs);
+    stack(s.O, s.n, Os);
+    if ((st = upload_csr(s.A, s.dA)) != QTL_OK || (st = upload_csr(Cs, s.dC)) != QTL_OK ||
+        (st = upload_csr(Os, s.dO)) != QTL_OK) {
+        qtl_system_free(sys);
+        return st;
+    }
+    *out = sys;
+    return QTL_OK;
+}
+
+int32_t qtl_system_dim(const qtl_system* sys) { return sys ? sys->s.n : 0; }
+
+int64_t qtl_system_liouvillian_nnz(const qtl_system* sys) { return sys ? sys->s.dL.nnz : 0; }
+
+qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_t is_ket,
+                             const double* tlist_dev, int32_t nt, const qtl_opts* opts,
+                             qtl_c128* expect_dev, qtl_c128* states_dev, qtl_device_info* info_dev) {
+    if (!sys || !state0_dev || !tlist_dev || nt < 1 || !info_dev) return QTL_EINVAL;
+    if (sys->s.n_e > 0 && !expect_dev) return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    System& s = sys->s;
+    if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    const int L = s.n * s.n;
+    // Largest number of Liouvillian entries in one CTA's rows (CTA c owns the
+    // rows r = c mod C): sizes the shared-memory copy of the operator.
+    int C = 0, rpt = 0;
+    if (!me_plan(L, opts->cluster_size, &C, &rpt)) return QTL_ETOOBIG;
+    std::vector<int64_t> per(C, 0);
+    for (int r = 0; r < L; ++r) per[r % C] += s.L_rp[r + 1] - s.L_rp[r];
+    const int64_t need = *std::max_element(per.begin(), per.end());
+    if (need > me_smem_nnz_budget(opts->precision, rpt)) return QTL_ETOOBIG;
+    char* scratch = nullptr;
+    const size_t epart_bytes = (size_t)nt * C * 2 * (s.n_e > 0 ? s.n_e : 1) * sizeof(double);
+    const size_t bytes = epart_bytes + sizeof(MeJob) + 512;
+    QTL_CUDA(cudaMallocAsync((void**)&scratch, bytes, stream));
+    MeJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.n = s.n;
+    J.L = L;
+    J.seg = s.dL.seg;
+    J.ci = s.dL.ci;
+    J.lv64 = s.dL.v64;
+    J.lv32 = s.dL.v32;
+    J.n_e = s.n_e;
+    J.ew = s.ew;
+    J.tlist = tlist_dev;
+    J.nt = nt;
+    J.state0 = (const double2*)state0_dev;
+    J.is_ket = is_ket ? 1 : 0;
+    J.epart = (double*)scratch;
+    MeJob* jd = (MeJob*)(scratch + ((epart_bytes + 255) & ~(size_t)255));
+    J.expect = (double2*)expect_dev;
+    J.states = (double2*)states_dev;
+    J.info = info_dev;
+    J.rtol = opts->rtol;
+    J.atol = opts->atol;
+    J.dt0 = opts->dt0;
+    J.dt_min = opts->dt_min;
+    J.dt_fixed = opts->dt_fixed;
+    J.max_steps = opts->max_steps;
+    J.fixed = opts->fixed_step ? 1 : 0;
+    J.method = opts->method;
+    J.smem_nnz = (int)need;
+    QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
+    QTL_CUDA(cudaMemcpyAsync(jd, &J, sizeof(J), cudaMemcpyHostToDevice, stream));
+    cudaError_t e = launch_me_cluster(jd, 1, L, J.smem_nnz, opts->precision, opts->cluster_size, stream);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        cudaFreeAsync(scratch, stream);
+        return e == cudaErrorInvalidValue ? QTL_ETOOBIG : QTL_ECUDA;
+    }
+    QTL_CUDA(cudaFreeAsync(scratch, stream));
+    return QTL_OK;
+}
+
+qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket, const double* tlist,
+                       int32_t nt, const qtl_opts* opts, qtl_c128* expect_out, qtl_c128* states_out,
+                       qtl_stats* stats) {
+    if (!sys || !state0) return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    System& s = sys->s;
+    if (s.n_e > 0 && !expect_out) return QTL_EINVAL;
+    const size_t n0 = is_ket ? (size_t)s.n : (size_t)s.n * s.n;
+    for (size_t i = 0; i < n0; ++i)
+        if (!finite_c(state0[i])) return QTL_EINVAL;
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    const size_t L = (size_t)s.n * s.n;
+    const size_t ne = (size_t)s.n_e * nt;
+    char* buf = nullptr;
+    const size_t bytes = n0 * 16 + (size_t)nt * 8 + ne * 16 + (states_out ? (size_t)nt * L * 16 : 0) +
+                         sizeof(qtl_device_info) + 5 * 256;
+    QTL_CUDA(cudaMallocAsync((void**)&buf, bytes, stream));
+    size_t off = 0;
+    auto carve = [&](size_t b) {
+        char* p = buf + off;
+        off = (off + b + 255) & ~(size_t)255;
+        return p;
+    };
+    qtl_c128* d_state = (qtl_c128*)carve(n0 * 16);
+    double* d_tl = (double*)carve((size_t)nt * 8);
+    qtl_c128* d_ex = (qtl_c128*)carve(ne * 16);
+    qtl_c128* d_states = states_out ? (qtl_c128*)carve((size_t)nt * L * 16) : nullptr;
+    qtl_device_info* d_info = (qtl_device_info*)carve(sizeof(qtl_device_info));
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_state, state0, n0 * 16, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_tl, tlist, (size_t)nt * 8, cudaMemcpyHostToDevice, stream)) != cudaSuccess) {
+        set_cuda_error(e);
+        cudaFreeAsync(buf, stream);
+        return QTL_ECUDA;
+    }
+    if (ne) cudaMemsetAsync(d_ex, 0, ne * 16, stream);
+    st = qtl_mesolve_async(sys, d_state, is_ket, d_tl, nt, opts, d_ex, d_states, d_info);
+    if (st != QTL_OK) {
+        cudaFreeAsync(buf, stream);
+        return st;
+    }
+    qtl_device_info info;
+    if (ne) QTL_CUDA(cudaMemcpyAsync(expect_out, d_ex, ne * 16, cudaMemcpyDeviceToHost, stream));
+    if (states_out)
+        QTL_CUDA(cudaMemcpyAsync(states_out, d_states, (size_t)nt * L * 16, cudaMemcpyDeviceToHost, stream));
+    QTL_CUDA(cudaMemcpyAsync(&info, d_info, sizeof(info), cudaMemcpyDeviceToHost, stream));
+    QTL_CUDA(cudaFreeAsync(buf, stream));
+    QTL_CUDA(cudaStreamSynchronize(stream));
+    if (stats) {
+        stats->steps_acc = info.steps_acc;
+        stats->steps_rej = info.steps_rej;
+        stats->rhs_evals = info.rhs_evals;
+        stats->jumps = info.jumps;
+    }
+    return (qtl_status)info.status;
+}
+
+qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const double* tlist_dev,
+                             int32_t nt, int32_t ntraj, uint64_t seed, int64_t traj_offset,
+                             const qtl_opts* opts, qtl_c128* expect_dev, qtl_c128* traj_expect_dev,
+                             qtl_device_info* info_dev) {
+    if (!sys || !psi0_dev || !tlist_dev || nt < 1 || ntraj < 1 || !info_dev || traj_offset < 0)
+        return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    System& s = sys->s;
+    if (s.n_e > 0 && !expect_dev) return QTL_EINVAL;
+    if (s.n > mc_traj_capacity()) return QTL_ETOOBIG;
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    const size_t ne = (size_t)s.n_e * nt;
+    double2* scratch = nullptr;
+    if (!traj_expect_dev && ne > 0) {
+        QTL_CUDA(cudaMallocAsync((void**)&scratch, ne * ntraj * sizeof(double2), stream));
+    }
+    McJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.n = s.n;
+    J.a_nnz = (int)s.dA.nnz;
+    J.aseg = s.dA.seg;
+    J.arp = s.dA.rp;
+    J.aci = s.dA.ci;
+    J.av64 = s.dA.v64;
+    J.av32 = s.dA.v32;
+    J.n_c = s.n_c;
+    J.crp = s.dC.rp;
+    J.cci = s.dC.ci;
+    J.cv = s.dC.v64;
+    J.n_e = s.n_e;
+    J.orp = s.dO.rp;
+    J.oci = s.dO.ci;
+    J.ov = s.dO.v64;
+    J.tlist = tlist_dev;
+    J.nt = nt;
+    J.psi0 = (const double2*)psi0_dev;
+    J.ntraj = ntraj;
+    J.seed = seed;
+    J.traj_offset = traj_offset;
+    J.traj_expect = traj_expect_dev ? (double2*)traj_expect_dev : scratch;
+    J.expect = (double2*)expect_dev;
+    J.info = info_dev;
+    J.rtol = opts->rtol;
+    J.atol = opts->atol;
+    J.dt0 = opts->dt0;
+    J.dt_min = opts->dt_min;
+    J.dt_fixed = opts->dt_fixed;
+    J.max_steps = opts->max_steps;
+    J.fixed = opts->fixed_step ? 1 : 0;
+    J.method = opts->method;
+    QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
+    cudaError_t e = launch_mc_traj(J, opts->precision, stream);
+    if (e == cudaSuccess) e = launch_mc_reduce(J, stream);
+    if (scratch) cudaFreeAsync(scratch, stream);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return QTL_ECUDA;
+    }
+    return QTL_OK;
+}
+
+qtl_status qtl_mcsolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                       int32_t ntraj, uint64_t seed, int64_t traj_offset, const qtl_opts* opts,
+                       qtl_c128* expect_out, qtl_c128* traj_expect_out, qtl_stats* stats) {
+    if (!sys || !psi0) return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    System& s = sys->s;
+    if (ntraj < 1 || (s.n_e > 0 && !expect_out)) return QTL_EINVAL;
+    for (int i = 0; i < s.n; ++i)
+        if (!finite_c(psi0[i])) return QTL_EINVAL;
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    const size_t ne = (size_t)s.n_e * nt;
+    char* buf = nullptr;
+    const size_t bytes = (size_t)s.n * 16 + (size_t)nt * 8 + ne * 16 + ne * ntraj * 16 +
+                         sizeof(qtl_device_info) + 5 * 256;
+    QTL_CUDA(cudaMallocAsync((void**)&buf, bytes, stream));
+    size_t off = 0;
+    auto carve = [&](size_t b) {
+        char* p = buf + off;
+        off = (off + b + 255) & ~(size_t)255;
+        return p;
+    };
+    qtl_c128* d_psi = (qtl_c128*)carve((size_t)s.n * 16);
+    double* d_tl = (double*)carve((size_t)nt * 8);
+    qtl_c128* d_ex = (qtl_c128*)carve(ne * 16);
+    qtl_c128* d_tex = (qtl_c128*)carve(ne * ntraj * 16);
+    qtl_device_info* d_info = (qtl_device_info*)carve(sizeof(qtl_device_info));
+    QTL_CUDA(cudaMemcpyAsync(d_psi, psi0, (size_t)s.n * 16, cudaMemcpyHostToDevice, stream));
+    QTL_CUDA(cudaMemcpyAsync(d_tl, tlist, (size_t)nt * 8, cudaMemcpyHostToDevice, stream));
+    st = qtl_mcsolve_async(sys, d_psi, d_tl, nt, ntraj, seed, traj_offset, opts, d_ex, d_tex, d_info);
+    if (st != QTL_OK) {
+        cudaFreeAsync(buf, stream);
+        return st;
+    }
+    qtl_device_info info;
+    if (ne) QTL_CUDA(cudaMemcpyAsync(expect_out, d_ex, ne * 16, cudaMemcpyDeviceToHost, stream));
+    if (traj_expect_out && ne)
+        QTL_CUDA(cudaMemcpyAsync(traj_expect_out, d_tex, ne * ntraj * 16, cudaMemcpyDeviceToHost, stream));
+    QTL_CUDA(cudaMemcpyAsync(&info, d_info, sizeof(info), cudaMemcpyDeviceToHost, stream));
+    QTL_CUDA(cudaFreeAsync(buf, stream));
+    QTL_CUDA(cudaStreamSynchronize(stream));
+    if (stats) {
+        stats->steps_acc = info.steps_acc;
+        stats->steps_rej = info.steps_rej;
+        stats->rhs_evals = info.rhs_evals;
+        stats->jumps = info.jumps;
+    }
+    return (qtl_status)info.status;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+"""ctypes binding of the C ABI declared in include/qtl.h.
+
+Argument marshalling only: every step of the solve runs in the library's
+CUDA kernels.  The names mirror the C entry points without the `qtl_` prefix
+(system_create, system_free, mesolve, mesolve_async, mcsolve, mcsolve_async,
+opts_default, strerror, launch_count).  There is no CPU fallback: if the
+library is missing or cannot be loaded, `load()` raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libqtl.so")
+
+QTL_OK, QTL_EINVAL, QTL_ENOMEM, QTL_ESTEP, QTL_ECUDA, QTL_ECANCEL, QTL_EBUSY, QTL_ETOOBIG = range(8)
+METHODS = {"dp5": 0, "tsit5": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+
+
+class QtlError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} (status {status})"
+                         + (f" [{last_cuda_error()}]" if status == QTL_ECUDA else ""))
+
+
+class Op(C.Structure):
+    _fields_ = [("n", C.c_int32), ("is_csr", C.c_int32), ("nnz", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("vals", C.c_void_p)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("precision", C.c_int32), ("rtol", C.c_double),
+                ("atol", C.c_double), ("dt0", C.c_double), ("dt_min", C.c_double),
+                ("max_steps", C.c_int64), ("fixed_step", C.c_int32), ("cluster_size", C.c_int32),
+                ("dt_fixed", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps_acc", C.c_int64), ("steps_rej", C.c_int64), ("rhs_evals", C.c_int64),
+                ("jumps", C.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class DeviceInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("steps_acc", C.c_int64),
+                ("steps_rej", C.c_int64), ("rhs_evals", C.c_int64), ("jumps", C.c_int64)]
+
+
+DEVICE_INFO_BYTES = C.sizeof(DeviceInfo)
+_lib = None
+
+
+def load():
+    """Loads libqtl.so (built in-tree by build.py); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libqtl.so not built ({LIB_PATH}); run paper_2504_21440_gb300/build.py")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    lib.qtl_opts_default.argtypes = [C.POINTER(Opts)]
+    lib.qtl_opts_default.restype = None
+    lib.qtl_system_create.argtypes = [C.POINTER(Op), C.POINTER(Op), C.c_int32, C.POINTER(Op),
+                                      C.c_int32, C.POINTER(P)]
+    lib.qtl_system_create.restype = C.c_int
+    lib.qtl_system_free.argtypes = [P]
+    lib.qtl_system_free.restype = None
+    lib.qtl_system_dim.argtypes = [P]
+    lib.qtl_system_dim.restype = C.c_int32
+    lib.qtl_system_liouvillian_nnz.argtypes = [P]
+    lib.qtl_system_liouvillian_nnz.restype = C.c_int64
+    lib.qtl_mesolve.argtypes = [P, P, C.c_int32, P, C.c_int32, C.POINTER(Opts), P, P,
+                                C.POINTER(Stats)]
+    lib.qtl_mesolve.restype = C.c_int
+    lib.qtl_mesolve_async.argtypes = [P, P, C.c_int32, P, C.c_int32, C.POINTER(Opts), P, P, P]
+    lib.qtl_mesolve_async.restype = C.c_int
+    lib.qtl_mcsolve.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_int64,
+                                C.POINTER(Opts), P, P, C.POINTER(Stats)]
+    lib.qtl_mcsolve.restype = C.c_int
+    lib.qtl_mcsolve_async.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_int64,
+                                      C.POINTER(Opts), P, P, P]
+    lib.qtl_mcsolve_async.restype = C.c_int
+    lib.qtl_strerror.argtypes = [C.c_int]
+    lib.qtl_strerror.restype = C.c_char_p
+    lib.qtl_last_cuda_error.argtypes = []
+    lib.qtl_last_cuda_error.restype = C.c_char_p
+    lib.qtl_launch_count.argtypes = []
+    lib.qtl_launch_count.restype = C.c_int64
+    _lib = lib
+    return lib
+
+
+def strerror(status):
+    return load().qtl_strerror(int(status)).decode()
+
+
+def last_cuda_error():
+    return load().qtl_last_cuda_error().decode()
+
+
+def launch_count():
+    return int(load().qtl_launch_count())
+
+
+def opts_default():
+    o = Opts()
+    load().qtl_opts_default(C.byref(o))
+    return o
+
+
+def make_opts(method="tsit5", precision="fp64", rtol=1e-8, atol=1e-10, dt0=0.0, dt_min=0.0,
+              max_steps=10_000_000, fixed_dt=None, cluster_size=0, stream=None):
+    o = opts_default()
+    o.method = METHODS[method]
+    o.precision = PRECISIONS[precision]
+    o.rtol, o.atol, o.dt0, o.dt_min = float(rtol), float(atol), float(dt0), float(dt_min)
+    o.max_steps = int(max_steps)
+    o.fixed_step = 1 if fixed_dt is not None else 0
+    o.dt_fixed = float(fixed_dt) if fixed_dt is not None else 0.0
+    o.cluster_size = int(cluster_size)
+    o.cuda_stream = stream
+    return o
+
+
+def _check(status, what):
+    if status != QTL_OK:
+        raise QtlError(status, what)
+
+
+class _OpHolder:
+    """Keeps the arrays behind a qtl_op alive for the duration of a call."""
+
+    def __init__(self, m):
+        if hasattr(m, "tocsr"):
+            m = m.tocsr()
+            self.rp = np.ascontiguousarray(m.indptr, dtype=np.int32)
+            self.ci = np.ascontiguousarray(m.indices, dtype=np.int32)
+            self.v = np.ascontiguousarray(m.data, dtype=np.complex128)
+            self.op = Op(m.shape[0], 1, len(self.v), self.rp.ctypes.data, self.ci.ctypes.data,
+                         self.v.ctypes.data)
+        else:
+            a = np.asarray(m, dtype=np.complex128)
+            self.v = np.asfortranarray(a)
+            self.op = Op(a.shape[0], 0, 0, None, None, self.v.ctypes.data)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def system_create(H, c_ops=(), e_ops=()):
+    """qtl_system_create: H, c_ops, e_ops as scipy sparse or dense arrays."""
+    lib = load()
+    hold = [_OpHolder(H)] + [_OpHolder(c) for c in c_ops] + [_OpHolder(e) for e in e_ops]
+    nc, ne = len(c_ops), len(e_ops)
+    ca = (Op * max(nc, 1))(*[h.op for h in hold[1:1 + nc]])
+    ea = (Op * max(ne, 1))(*[h.op for h in hold[1 + nc:]])
+    out = C.c_void_p()
+    _check(lib.qtl_system_create(C.byref(hold[0].op), ca, nc, ea, ne, C.byref(out)),
+           "qtl_system_create")
+    return out
+
+
+def system_free(sys):
+    load().qtl_system_free(sys)
+
+
+def system_dim(sys):
+    return int(load().qtl_system_dim(sys))
+
+
+def system_liouvillian_nnz(sys):
+    return int(load().qtl_system_liouvillian_nnz(sys))
+
+
+def mesolve(sys, n_e, state0, tlist, opts, save_states=False):
+    """qtl_mesolve with host arrays.  Returns dict(expect[n_e, nt], states, stats)."""
+    lib = load()
+    s0 = np.ascontiguousarray(state0, dtype=np.complex128)
+    is_ket = 1 if s0.ndim == 1 else 0
+    if not is_ket:
+        s0 = np.ascontiguousarray(s0.reshape(-1, order="F"))
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt = len(tl)
+    n = system_dim(sys)
+    ex = np.zeros((max(n_e, 1), nt), dtype=np.complex128)
+    states = np.zeros((nt, n * n), dtype=np.complex128) if save_states else None
+    st = Stats()
+    status = lib.qtl_mesolve(sys, _ptr(s0), is_ket, _ptr(tl), nt, C.byref(opts), _ptr(ex),
+                             _ptr(states), C.byref(st))
+    _check(status, "qtl_mesolve")
+    out = dict(expect=ex[:n_e], stats=st.as_dict(), states=None)
+    if states is not None:
+        out["states"] = states.reshape(nt, n, n).transpose(0, 2, 1).copy()
+    return out
+
+
+def mesolve_async(sys, state0_dev, is_ket, tlist_dev, opts, expect_dev, states_dev, info_dev):
+    """qtl_mesolve_async with device tensors (torch) on opts.cuda_stream."""
+    _check(load().qtl_mesolve_async(sys, _ptr(state0_dev), int(is_ket), _ptr(tlist_dev),
+                                    int(tlist_dev.numel()), C.byref(opts), _ptr(expect_dev),
+                                    _ptr(states_dev), _ptr(info_dev)), "qtl_mesolve_async")
+
+
+def mcsolve(sys, n_e, psi0, tlist, ntraj, seed, opts, traj_offset=0, keep_trajectories=False):
+    """qtl_mcsolve with host arrays.  Returns dict(expect, traj_expect?, stats)."""
+    lib = load()
+    p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt = len(tl)
+    ex = np.zeros((max(n_e, 1), nt), dtype=np.complex128)
+    tex = np.zeros((max(n_e, 1), nt, ntraj), dtype=np.complex128) if keep_trajectories else None
+    st = Stats()
+    status = lib.qtl_mcsolve(sys, _ptr(p0), _ptr(tl), nt, int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
+                             int(traj_offset), C.byref(opts), _ptr(ex), _ptr(tex), C.byref(st))
+    _check(status, "qtl_mcsolve")
+    out = dict(expect=ex[:n_e], stats=st.as_dict())
+    if tex is not None:
+        out["traj_expect"] = np.moveaxis(tex[:n_e], 2, 0)   # [traj, e, t]
+    return out
+
+
+def mcsolve_async(sys, psi0_dev, tlist_dev, ntraj, seed, opts, expect_dev, traj_expect_dev,
+                  info_dev, traj_offset=0):
+    _check(load().qtl_mcsolve_async(sys, _ptr(psi0_dev), _ptr(tlist_dev), int(tlist_dev.numel()),
+                                    int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
+                                    int(traj_offset), C.byref(opts), _ptr(expect_dev),
+                                    _ptr(traj_expect_dev), _ptr(info_dev)), "qtl_mcsolve_async")
+
+
+class System:
+    """Owning wrapper: System(H, c_ops, e_ops) -> .mesolve(...) / .mcsolve(...)."""
+
+    def __init__(self, H, c_ops=(), e_ops=()):
+        self.handle = system_create(H, c_ops, e_ops)
+        self.n = system_dim(self.handle)
+        self.n_e = len(e_ops)
+        self.n_c = len(c_ops)
+
+    def mesolve(self, state0, tlist, save_states=False, **kw):
+        return mesolve(self.handle, self.n_e, state0, tlist, make_opts(**kw), save_states)
+
+    def mcsolve(self, psi0, tlist, ntraj, seed, traj_offset=0, keep_trajectories=False, **kw):
+        return mcsolve(self.handle, self.n_e, psi0, tlist, ntraj, seed, make_opts(**kw),
+                       traj_offset, keep_trajectories)
+
+    def free(self):
+        if self.handle:
+            system_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

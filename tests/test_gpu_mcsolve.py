@@ -1,0 +1,108 @@
+"""GPU parity of mcsolve (trajectory kernel, through the C ABI) against the
+FP64 oracle, trajectory by trajectory, plus ensemble statistics."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.mcsolve import mcsolve as oracle_mcsolve
+from oracle.mesolve import mesolve as oracle_mesolve
+from oracle.philox import uniform
+from tests.gpu_util import maxabs, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(s, tlist, ntraj, seed, **kw):
+    qtl = require_gpu()
+    keep = kw.pop("keep_trajectories", True)
+    off = kw.pop("traj_offset", 0)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    try:
+        return g.mcsolve(s.psi0, tlist, ntraj, seed, traj_offset=off, keep_trajectories=keep, **kw)
+    finally:
+        g.free()
+
+
+def test_two_level_jump_times_closed_form():
+    """H = 0: psi stays |e> (normalised) until t* = -ln(r)/g, then |g>."""
+    g_ = 0.5
+    s = W.two_level_decay(gamma=g_, t_end=8.0, nt=81)
+    got = _gpu(s, s.tlist, 200, 11, rtol=1e-11, atol=1e-13)
+    pe = got["traj_expect"][:, 0, :].real
+    for j in range(200):
+        t_star = -math.log(uniform(11, j, 0)) / g_
+        expect = (s.tlist < t_star - 1e-7).astype(float)
+        mask = np.abs(s.tlist - t_star) > 1e-7
+        assert np.max(np.abs(pe[j][mask] - expect[mask])) < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64"])
+def test_trajectory_parity_jc(precision):
+    s = W.jaynes_cummings(N=5, nt=41, t_end=80.0, kappa=0.1, gamma=0.05)
+    ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=24, seed=7,
+                         keep_trajectories=True)
+    got = _gpu(s, s.tlist, 24, 7, precision=precision)
+    assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-8
+    assert maxabs(got["expect"], ref["expect"]) <= 1e-8
+    assert got["stats"]["jumps"] == ref["stats"]["jumps"]
+
+
+def test_trajectory_parity_fixed_step_fock_cascade():
+    s = W.damped_oscillator(N=6, omega=1.3, gamma=0.3, n0=3, t_end=12.0, nt=25)
+    ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=16, seed=2024,
+                         fixed_dt=0.01, keep_trajectories=True)
+    got = _gpu(s, s.tlist, 16, 2024, fixed_dt=0.01)
+    assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-8
+
+
+def test_traj_offset_selects_the_same_streams():
+    s = W.jaynes_cummings(N=4, nt=11, t_end=40.0, kappa=0.2)
+    a = _gpu(s, s.tlist, 40, 3)
+    b = _gpu(s, s.tlist, 20, 3, traj_offset=20)
+    assert maxabs(a["traj_expect"][20:], b["traj_expect"]) == 0.0
+
+
+def test_ensemble_matches_mesolve_jc_config():
+    """The configured JC cavity (N=40 x 2) with 1000 trajectories: the mean is
+    within 3 sigma/sqrt(ntraj) of the master equation at every time."""
+    s = W.jaynes_cummings(nt=200)
+    me = oracle_mesolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist)
+    got = _gpu(s, s.tlist, 1000, 1)
+    per = got["traj_expect"].real
+    sd = per.std(axis=0)
+    bound = 3 * np.maximum(sd, 1e-3) / math.sqrt(1000) + 1e-6
+    assert np.all(np.abs(got["expect"].real - me["expect"].real) <= bound)
+
+
+def test_mixed_precision_trajectories():
+    s = W.jaynes_cummings(N=5, nt=41, t_end=80.0, kappa=0.1, gamma=0.05)
+    ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=24, seed=7,
+                         keep_trajectories=True)
+    got = _gpu(s, s.tlist, 24, 7, precision="mixed", rtol=1e-7, atol=1e-9)
+    # a jump time moves by the FP32 rounding of the norm; compare trajectories
+    # whose jump counts agree, at the 1e-6 bar
+    assert maxabs(got["expect"], ref["expect"]) <= 5e-2
+    same = [j for j in range(24) if np.allclose(got["traj_expect"][j, 0, -1].real,
+                                                ref["traj_expect"][j, 0, -1].real, atol=1e-3)]
+    assert len(same) >= 20
+    for j in same:
+        assert maxabs(got["traj_expect"][j], ref["traj_expect"][j]) <= 1e-5
+
+
+def test_mcsolve_edge_cases():
+    qtl = require_gpu()
+    s = W.two_level_decay()
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    one = g.mcsolve(s.psi0, np.array([0.0]), 3, 1)
+    assert maxabs(one["expect"][0], [1.0]) < 1e-15
+    with pytest.raises(qtl.QtlError):
+        g.mcsolve(s.psi0, np.array([0.0, 2.0, 1.0]), 3, 1)
+    g.free()
+    # no collapse operators: no jumps, the state evolves unitarily
+    g2 = qtl.System(W.sigmax(), [], [W.sigmaz()])
+    out = g2.mcsolve(W.fock(2, 0), np.linspace(0, 3, 7), 4, 1, rtol=1e-10, atol=1e-12)
+    assert out["stats"]["jumps"] == 0
+    assert maxabs(out["expect"][0].real, np.cos(2 * np.linspace(0, 3, 7))) < 1e-8
+    g2.free()
