@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Benchmark of the Lindblad / quantum-trajectory hot path on GB300.
+
+Workload (default `jc_40x2`): the Jaynes-Cummings cavity (x) qubit, N = 40 x 2
+(Hilbert dimension 80, Liouvillian 6400 x 6400 CSR), H = wc a'a + wq sz/2 +
+g (a s+ + a' s-) with g = 0.1, wc = wq = 1, C = sqrt(0.05) a and
+sqrt(0.02) s-, rho0 = |0> (x) |e>, tlist = range(0, 10 pi / g, 1000),
+Tsit5 with rtol 1e-8, atol 1e-10, all in FP64.  One step is one pass of the
+whole path over this job: one mesolve (Liouvillian RHS, adaptive RK 5(4),
+expectation values) and one mcsolve with 1000 trajectories (Philox stream
+seed 1), the two solves running concurrently on two CUDA streams.
+
+Printed (rank 0, one JSON line): Lindblad RHS evaluations per second of the
+whole job, with trajectories per second and p50/p99 job latency beside it,
+a roofline object for the dominant kernel, the FP64 oracle timed on the host
+cores (cpu_baseline), and the same metric end to end through the C ABI with
+host buffers (e2e).
+
+Under torchrun each rank runs the same job on its own GPU (independent
+problems, no collective on the data path): weak scaling.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this comparison).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+NTRAJ = 1000
+SEED = 1
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2: written between timed steps
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="qtl", choices=["qtl", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    s = W.jaynes_cummings()   # N = 40 x 2, tlist range(0, 10 pi/g, 1000)
+    return s
+
+
+def algorithmic_flops(nnz, n_rows, stats):
+    """FP64 flops of the integrator counted from the work done: a complex
+    multiply-add is 8 flops per stored operator entry per RHS evaluation;
+    each attempted step forms 21 stage increments and 7 error terms, each a
+    real-times-complex product added to a complex entry (4 flops) per row."""
+    attempts = stats["steps_acc"] + stats["steps_rej"]
+    return 8.0 * nnz * stats["rhs_evals"] + 4.0 * 28 * n_rows * attempts
+
+
+def traffic_from_profile(kernel_src, summary):
+    """DRAM bytes per launch recorded by an ncu capture (profiles/*.md), or
+    None when the kernel source changed since the counters were taken."""
+    import hashlib
+    try:
+        src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        txt = open(summary).read()
+    except OSError:
+        return None
+    fields = dict(l.split(":", 1) for l in txt.splitlines() if l.startswith(("source_sha256_16:", "dram_bytes_per_launch:")))
+    if fields.get("source_sha256_16:".rstrip(":"), "").strip() != src_hash:
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_oracle_sample(s, ntraj_sample):
+    """The FP64 oracle, as it stands, on the same job: the full mesolve and
+    `ntraj_sample` of the 1000 trajectories, single-threaded."""
+    from oracle.mcsolve import mcsolve as o_mc
+    from oracle.mesolve import mesolve as o_me
+    t0 = time.perf_counter()
+    me = o_me(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, method="tsit5", rtol=s.rtol, atol=s.atol)
+    t1 = time.perf_counter()
+    o_mc(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=ntraj_sample, seed=SEED,
+         rtol=s.rtol, atol=s.atol)
+    t2 = time.perf_counter()
+    job_s = (t1 - t0) + (t2 - t1) * NTRAJ / ntraj_sample
+    return dict(value=me["stats"]["rhs_evals"] / job_s, me_s=t1 - t0, mc_s=t2 - t1,
+                job_s=job_s, expect=me["expect"], rhs=me["stats"]["rhs_evals"])
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    s = workload()
+    ntr = 2
+    for _ in range(args.warmup):
+        cpu_oracle_sample(s, ntr)
+    vals, jobs = [], []
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(s, ntr)
+        vals.append(r["value"])
+        jobs.append(r["job_s"])
+    v = statistics.mean(vals)
+    sample = (f"per step: oracle mesolve of the full job ({r['rhs']} RHS evaluations) + "
+              f"{ntr} of {NTRAJ} trajectories, trajectory time scaled to {NTRAJ}")
+    out = {"metric": "Lindblad RHS evals/s (mesolve + concurrent 1000-trajectory mcsolve job)",
+           "value": v, "unit": "RHS evals/s", "impl": "reference", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(jobs),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "jc_40x2 (N=40 x 2, L=6400) mesolve FP64 + mcsolve 1000 traj FP64"},
+           "cpu_baseline": {"value": v, "unit": "RHS evals/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": "RHS evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_qtl(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2504_21440_gb300 import qtl
+    qtl.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    s = workload()
+    n_e, nt = len(s.e_ops), len(s.tlist)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    psi = torch.from_numpy(s.psi0).to(dev)
+    tl = torch.from_numpy(s.tlist).to(dev)
+    ex_me = torch.zeros((n_e, nt), dtype=torch.complex128, device=dev)
+    ex_mc = torch.zeros((n_e, nt), dtype=torch.complex128, device=dev)
+    tex = torch.zeros((n_e, nt, NTRAJ), dtype=torch.complex128, device=dev)
+    info_me = torch.zeros(5, dtype=torch.int64, device=dev)
+    info_mc = torch.zeros(5, dtype=torch.int64, device=dev)
+    st_me, st_mc = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    tol = dict(method="tsit5", precision="fp64", rtol=s.rtol, atol=s.atol)
+    o_me = qtl.make_opts(stream=st_me.cuda_stream, **tol)
+    o_mc = qtl.make_opts(stream=st_mc.cuda_stream, **tol)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    main = torch.cuda.current_stream(dev)
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(main)
+        st_me.wait_event(e[0])
+        st_mc.wait_event(e[0])
+        e[1].record(st_me)
+        qtl.mesolve_async(g.handle, psi, 1, tl, o_me, ex_me, None, info_me)
+        e[2].record(st_me)
+        e[3].record(st_mc)
+        qtl.mcsolve_async(g.handle, psi, tl, NTRAJ, SEED, o_mc, ex_mc, tex, info_mc)
+        e[4].record(st_mc)
+        return e
+
+    for _ in range(args.warmup):
+        step()
+        torch.cuda.synchronize(dev)
+    nnz_L, nnz_A = qtl.system_nnz(g.handle, 2), qtl.system_nnz(g.handle, 1)
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = qtl.launch_count()
+    job_ms, me_ms, mc_ms = [], [], []
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e = step()
+        torch.cuda.synchronize(dev)
+        me_ms.append(e[1].elapsed_time(e[2]))
+        mc_ms.append(e[3].elapsed_time(e[4]))
+        job_ms.append(max(e[0].elapsed_time(e[2]), e[0].elapsed_time(e[4])))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t_wall0
+    launches = qtl.launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = sum(job_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    im = info_me.cpu().numpy()
+    ic = info_mc.cpu().numpy()
+    st_me_d = dict(steps_acc=int(im[1]), steps_rej=int(im[2]), rhs_evals=int(im[3]))
+    st_mc_d = dict(steps_acc=int(ic[1]), steps_rej=int(ic[2]), rhs_evals=int(ic[3]), jumps=int(ic[4]))
+    status = (int(im[0]) & 0xffffffff, int(ic[0]) & 0xffffffff)
+    ms_per_step = total_ms / args.steps
+    value = world * st_me_d["rhs_evals"] / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel (FP64 ALU bound)
+    fl_mc = algorithmic_flops(nnz_A, s.n, st_mc_d)
+    fl_me = algorithmic_flops(nnz_L, s.n * s.n, st_me_d)
+    k_me, k_mc = statistics.mean(me_ms), statistics.mean(mc_ms)
+    dom = "mc_traj_kernel" if k_mc >= k_me else "me_cluster_kernel"
+    fl, kms = (fl_mc, k_mc) if dom == "mc_traj_kernel" else (fl_me, k_me)
+    achieved = fl / (kms / 1e3) / 1e12
+    src = "mc_traj.cu" if dom == "mc_traj_kernel" else "me_cluster.cu"
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", src),
+                                   os.path.join(ROOT, "profiles", f"{dom}_jc40x2_fp64.md"))
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom,
+            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (FP64 pipe; nominal 1.25 TFLOP/s)"}
+    other = {"me_cluster_kernel": {"ms": k_me, "tflops": fl_me / (k_me / 1e3) / 1e12},
+             "mc_traj_kernel": {"ms": k_mc, "tflops": fl_mc / (k_mc / 1e3) / 1e12}}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        err = None
+        if not args.no_cpu_baseline:
+            r = cpu_oracle_sample(s, 8)
+            cpu = {"value": r["value"], "unit": "RHS evals/s", "cores": 1, "kind": "oracle",
+                   "sample": f"oracle mesolve of the full job ({r['me_s']:.1f} s) + 8 of {NTRAJ} "
+                             f"trajectories ({r['mc_s']:.1f} s), trajectory time scaled to {NTRAJ}; "
+                             "single-threaded NumPy/SciPy"}
+            err = float(np.max(np.abs(ex_me.cpu().numpy() - r["expect"])))
+        e2e = None
+        if not args.no_e2e:
+            e2e = run_e2e(qtl, g, s, dev, args.steps)
+        sj = sorted(job_ms)
+        out = {"metric": "Lindblad RHS evals/s (mesolve + concurrent 1000-trajectory mcsolve job)",
+               "value": value, "unit": "RHS evals/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": "jc_40x2 (N=40 x 2, Liouvillian 6400x6400, nnz %d) mesolve "
+                                      "FP64 Tsit5 rtol 1e-8 atol 1e-10, 1000 saveat + mcsolve 1000 "
+                                      "trajectories FP64, concurrent streams" % nnz_L,
+                          "l2": "flushed (512 MB write) between timed steps",
+                          "parallelism": f"independent job per GPU x{world}"},
+               "mcsolve_traj_per_s": world * NTRAJ / (ms_per_step / 1e3),
+               "latency_ms": {"p50": sj[len(sj) // 2], "p99": sj[min(len(sj) - 1, int(0.99 * len(sj)))],
+                              "mesolve_mean": k_me, "mcsolve_mean": k_mc},
+               "status": list(status), "stats": {"mesolve": st_me_d, "mcsolve": st_mc_d},
+               "err_vs_fp64_oracle": err, "roofline": roof, "kernels": other,
+               "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+               "wall_s": wall}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    g.free()
+
+
+def run_e2e(qtl, g, s, dev, steps):
+    """The same job through the host-pointer C ABI (qtl_mesolve and
+    qtl_mcsolve, one host thread each): every step copies psi0 and tlist to
+    the device and the expectation values back."""
+    import torch
+    st1, st2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    tol = dict(method="tsit5", precision="fp64", rtol=s.rtol, atol=s.atol)
+    o1 = qtl.make_opts(stream=st1.cuda_stream, **tol)
+    o2 = qtl.make_opts(stream=st2.cuda_stream, **tol)
+    n_e, nt = len(s.e_ops), len(s.tlist)
+    res = {}
+
+    def me():
+        res["me"] = qtl.mesolve(g.handle, n_e, s.psi0, s.tlist, o1)
+
+    def mc():
+        res["mc"] = qtl.mcsolve(g.handle, n_e, s.psi0, s.tlist, NTRAJ, SEED, o2)
+
+    walls = []
+    for k in range(steps + 1):
+        t0 = time.perf_counter()
+        a, b = threading.Thread(target=me), threading.Thread(target=mc)
+        a.start()
+        b.start()
+        a.join()
+        b.join()
+        if k > 0:
+            walls.append(time.perf_counter() - t0)
+    w = statistics.mean(walls)
+    h2d = 2 * (s.n * 16 + nt * 8)
+    d2h = 2 * (n_e * nt * 16 + 40)
+    return {"value": res["me"]["stats"]["rhs_evals"] / w, "unit": "RHS evals/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * w}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_qtl(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -140,10 +140,15 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c,
  * by _async calls on the system must have completed. */
 void qtl_system_free(qtl_system* sys);
 
-/* Hilbert dimension, number of collapse operators / observables, and the
- * number of stored entries of the Liouvillian (0 before it is built). */
+/* Hilbert dimension, and the number of stored entries of the Liouvillian
+ * (0 before a mesolve has built it). */
 int32_t qtl_system_dim(const qtl_system* sys);
 int64_t qtl_system_liouvillian_nnz(const qtl_system* sys);
+
+/* Stored entries of one of the system's operators: which = 0 for H, 1 for
+ * A = -i H_eff (the trajectory right-hand side), 2 for the Liouvillian (0
+ * before it is built).  -1 for a NULL system or an unknown `which`. */
+int64_t qtl_system_nnz(const qtl_system* sys, int32_t which);
 
 /* mesolve (Sec. 3.2): integrates d rho/dt = L rho from tlist[0].
  *   state0    is_ket = 1: psi0[n] (rho0 = |psi0><psi0|, ket2dm);

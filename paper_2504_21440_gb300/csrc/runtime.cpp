@@ -401,6 +401,16 @@ int32_t qtl_system_dim(const qtl_system* sys) { return sys ? sys->s.n : 0; }
 
 int64_t qtl_system_liouvillian_nnz(const qtl_system* sys) { return sys ? sys->s.dL.nnz : 0; }
 
+int64_t qtl_system_nnz(const qtl_system* sys, int32_t which) {
+    if (!sys) return -1;
+    switch (which) {
+        case 0: return sys->s.H.nnz();
+        case 1: return sys->s.A.nnz();
+        case 2: return sys->s.dL.nnz;
+    }
+    return -1;
+}
+
 qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_t is_ket,
                              const double* tlist_dev, int32_t nt, const qtl_opts* opts,
                              qtl_c128* expect_dev, qtl_c128* states_dev, qtl_device_info* info_dev) {

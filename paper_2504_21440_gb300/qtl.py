@@ -75,6 +75,8 @@ def load():
     lib.qtl_system_dim.restype = C.c_int32
     lib.qtl_system_liouvillian_nnz.argtypes = [P]
     lib.qtl_system_liouvillian_nnz.restype = C.c_int64
+    lib.qtl_system_nnz.argtypes = [P, C.c_int32]
+    lib.qtl_system_nnz.restype = C.c_int64
     lib.qtl_mesolve.argtypes = [P, P, C.c_int32, P, C.c_int32, C.POINTER(Opts), P, P,
                                 C.POINTER(Stats)]
     lib.qtl_mesolve.restype = C.c_int
@@ -181,6 +183,11 @@ def system_dim(sys):
 
 def system_liouvillian_nnz(sys):
     return int(load().qtl_system_liouvillian_nnz(sys))
+
+
+def system_nnz(sys, which):
+    """qtl_system_nnz: stored entries of H (0), A = -i H_eff (1), the Liouvillian (2)."""
+    return int(load().qtl_system_nnz(sys, int(which)))
 
 
 def mesolve(sys, n_e, state0, tlist, opts, save_states=False):
