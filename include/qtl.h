@@ -192,6 +192,40 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
                              const qtl_opts* opts, qtl_c128* expect_dev,
                              qtl_c128* traj_expect_dev, qtl_device_info* info_dev);
 
+/* No counterpart in the paper: an mcsolve entry point for callers that cannot
+ * allocate device memory while they solve -- code running during CUDA stream
+ * capture (cudaMalloc is not allowed there), processes whose device memory is
+ * owned by another allocator or a fixed budget, and latency-critical loops
+ * that must not wait on the driver's allocator.  It does what
+ * qtl_mcsolve_async does (same kernels, same results) but allocates nothing:
+ *   - every input is a caller-owned DEVICE array: A = -i H_eff as an n x n
+ *     CSR (row pointers a_row_ptr[n+1], column indices and complex values of
+ *     a_nnz entries), the n_c collapse operators stacked row-wise in one CSR
+ *     of n_c*n rows (operator k in rows k*n .. k*n+n-1), the n_e observables
+ *     stacked the same way, psi0[n] and tlist[nt];
+ *   - expect[n_e*nt] (trajectory means, row k = observable k) and info are
+ *     caller-owned device outputs;
+ *   - scratch (row segments, the complex64 copy of A for QTL_MIXED and the
+ *     n_e*nt*ntraj per-trajectory expectation values) lives in one
+ *     file-scope device array of QTL_NOALLOC_SCRATCH_BYTES (32 MiB) that the
+ *     library holds on every GPU that loads it until the process exits.
+ * Requests whose scratch would exceed that size return QTL_ETOOBIG; n is
+ * limited to 1024 (QTL_ETOOBIG above).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array, which keeps the previous call's contents: calls that overlap
+ * on the GPU race on it and must be ordered by the caller.  Enqueued on
+ * opts->cuda_stream; status in info->status as for the _async calls. */
+#define QTL_NOALLOC_SCRATCH_BYTES (32u << 20)
+qtl_status qtl_mcsolve_noalloc(int32_t n, const int32_t* a_row_ptr, const int32_t* a_col_idx,
+                               const qtl_c128* a_vals, int64_t a_nnz, int32_t n_c,
+                               const int32_t* c_row_ptr, const int32_t* c_col_idx,
+                               const qtl_c128* c_vals, int32_t n_e, const int32_t* o_row_ptr,
+                               const int32_t* o_col_idx, const qtl_c128* o_vals,
+                               const qtl_c128* psi0, const double* tlist, int32_t nt,
+                               int32_t ntraj, uint64_t seed, int64_t traj_offset,
+                               const qtl_opts* opts, qtl_c128* expect, qtl_device_info* info);
+
 /* Human-readable text of a status, and the last CUDA error seen by this
  * thread (empty string if none). */
 const char* qtl_strerror(qtl_status s);

@@ -117,6 +117,8 @@ cudaError_t launch_mc_traj(const McJob& job, int precision, cudaStream_t st);
 cudaError_t launch_mc_reduce(const McJob& job, cudaStream_t st);
 cudaError_t launch_info_init(qtl_device_info* info, cudaStream_t st);
 
+qtl_status validate_opts(const qtl_opts* o);
+
 int me_cluster_capacity();        // max L handled by the cluster kernel
 int mc_traj_capacity();           // max n handled by the trajectory kernel
 

@@ -297,6 +297,8 @@ static qtl_status check_opts(const qtl_opts* o) {
     return QTL_OK;
 }
 
+qtl_status validate_opts(const qtl_opts* o) { return check_opts(o); }
+
 static qtl_status check_tlist_host(const double* tl, int nt) {
     if (!tl || nt < 1) return QTL_EINVAL;
     for (int i = 0; i < nt; ++i) {

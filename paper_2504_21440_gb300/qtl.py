@@ -88,6 +88,10 @@ def load():
     lib.qtl_mcsolve_async.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_int64,
                                       C.POINTER(Opts), P, P, P]
     lib.qtl_mcsolve_async.restype = C.c_int
+    lib.qtl_mcsolve_noalloc.argtypes = [C.c_int32, P, P, P, C.c_int64, C.c_int32, P, P, P,
+                                        C.c_int32, P, P, P, P, P, C.c_int32, C.c_int32,
+                                        C.c_uint64, C.c_int64, C.POINTER(Opts), P, P]
+    lib.qtl_mcsolve_noalloc.restype = C.c_int
     lib.qtl_strerror.argtypes = [C.c_int]
     lib.qtl_strerror.restype = C.c_char_p
     lib.qtl_last_cuda_error.argtypes = []
@@ -243,6 +247,28 @@ def mcsolve_async(sys, psi0_dev, tlist_dev, ntraj, seed, opts, expect_dev, traj_
                                     int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
                                     int(traj_offset), C.byref(opts), _ptr(expect_dev),
                                     _ptr(traj_expect_dev), _ptr(info_dev)), "qtl_mcsolve_async")
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def mcsolve_noalloc(n, a_csr, c_csr, n_c, o_csr, n_e, psi0_dev, tlist_dev, ntraj, seed, opts,
+                    expect_dev, info_dev, traj_offset=0):
+    """qtl_mcsolve_noalloc: every operator is a tuple (row_ptr, col_idx, vals) of
+    device tensors (int32, int32, complex128); A = -i H_eff is n x n, the
+    collapse operators and observables are stacked row-wise.  Allocates
+    nothing on the device; enqueued on opts.cuda_stream."""
+    def parts(csr):
+        return (None, None, None) if csr is None else tuple(_ptr(x) for x in csr)
+    arp, aci, av = parts(a_csr)
+    crp, cci, cv = parts(c_csr)
+    orp, oci, ov = parts(o_csr)
+    _check(load().qtl_mcsolve_noalloc(int(n), arp, aci, av, int(a_csr[2].numel()), int(n_c), crp,
+                                      cci, cv, int(n_e), orp, oci, ov, _ptr(psi0_dev),
+                                      _ptr(tlist_dev), int(tlist_dev.numel()), int(ntraj),
+                                      C.c_uint64(int(seed) & (2**64 - 1)), int(traj_offset),
+                                      C.byref(opts), _ptr(expect_dev), _ptr(info_dev)),
+           "qtl_mcsolve_noalloc")
 
 
 class System:
