@@ -173,6 +173,28 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
                              qtl_c128* expect_dev, qtl_c128* states_dev,
                              qtl_device_info* info_dev);
 
+/* Batched mesolve for parameter sweeps (Sec. 3.2 applied to nb independent
+ * systems): nb solves sharing tlist and opts, each with its own system and
+ * initial state.  Each system gets the launch plan its own size implies --
+ * the smallest cluster C in {1, 2, 4, 8, 16} with C*1024 >= n^2, and the
+ * fewest rows per thread that cover n^2 with that C -- so a solve's
+ * arithmetic, and its result bit for bit, does not depend on what else is in
+ * the batch; it equals qtl_mesolve with opts->cluster_size = that C.  Solves
+ * with the same plan share one launch (clusters take solves dynamically,
+ * largest first); different plans run concurrently on streams forked from
+ * opts->cuda_stream and joined back into it.  opts->cluster_size is ignored.
+ *   _async: state0_dev[b], expect_dev[b] are device pointers held in host
+ *   arrays of nb entries; is_ket[b] host array; info_dev a device array of nb
+ *   qtl_device_info.  Host form: the same with host pointers, stats[b] (or
+ *   NULL), returning the first failing solve's status. */
+qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_t nb,
+                                   const qtl_c128* const* state0_dev, const int32_t* is_ket,
+                                   const double* tlist_dev, int32_t nt, const qtl_opts* opts,
+                                   qtl_c128* const* expect_dev, qtl_device_info* info_dev);
+qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb, const qtl_c128* const* state0,
+                             const int32_t* is_ket, const double* tlist, int32_t nt,
+                             const qtl_opts* opts, qtl_c128* const* expect_out, qtl_stats* stats);
+
 /* mcsolve (Sec. 3.3): ntraj trajectories from the ket psi0[n].
  *   seed      64-bit key of the per-trajectory Philox4x32-10 streams: draw d
  *             of trajectory j uses counter (d, traj_offset + j, 0, 0) and key

@@ -112,7 +112,7 @@ struct McJob {
 bool me_plan(int L_max, int cluster_size, int* C, int* rpt);
 int me_smem_nnz_budget(int precision, int rpt);
 cudaError_t launch_me_cluster(const MeJob* jobs_dev, int njobs, int L_max, int smem_nnz,
-                              int precision, int cluster_size, cudaStream_t st);
+                              int precision, int cluster_size, int* next, cudaStream_t st);
 cudaError_t launch_mc_traj(const McJob& job, int precision, cudaStream_t st);
 cudaError_t launch_mc_reduce(const McJob& job, cudaStream_t st);
 cudaError_t launch_info_init(qtl_device_info* info, cudaStream_t st);

@@ -189,6 +189,7 @@ enum { MC_STEP = 0, MC_REPEAT = 1, MC_DONE = 2 };
 // FP64 pipe is 1/64 rate, so no FP64 scalar work is replicated per thread).
 struct McCtl {
     double coef[28];  // htry * a_sj (21, packed by stage), htry * e_j (7)
+    float coeff[28];  // the same, rounded to FP32 (mixed precision)
     double inv;       // 1 / |C_k psi*| of the chosen channel
     int action, land, accept, save, ch, rootgo, pub;
     float wf[MC_TMAX / 32];
@@ -197,8 +198,8 @@ struct McCtl {
 
 __host__ __device__ constexpr int mc_coef_a(int s, int j) { return s * (s - 1) / 2 + j; }
 
-template <bool MIXED, int RPT, int MAXT>
-__global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
+template <bool MIXED, int RPT, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
     using T = typename MPrec<MIXED>::T;
     using T2 = typename MPrec<MIXED>::T2;
     using TV = T2;
@@ -240,20 +241,35 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
     for (int jt = blockIdx.x; jt < J.ntraj; jt += gridDim.x) {
         const unsigned long long traj = (unsigned long long)(J.traj_offset + jt);
         double2 y[RPT], ynew[RPT];
+        float2 yf[RPT], yfn[RPT];
         T2 k[7][RPT];
         bool own[RPT];
         int row[RPT];
+        auto coefT = [&](int i) -> T {
+            if constexpr (MIXED)
+                return cb.coeff[i];
+            else
+                return cb.coef[i];
+        };
+        auto sync_yf = [&]() {
+            if constexpr (MIXED) {
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) yf[m] = make_float2((float)y[m].x, (float)y[m].y);
+            }
+        };
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             row[m] = tid + m * T_;
             own[m] = row[m] < n;
             y[m] = own[m] ? J.psi0[row[m]] : make_double2(0.0, 0.0);
             ynew[m] = y[m];
+            yfn[m] = make_float2(0.f, 0.f);
             if (own[m]) {
                 yd[row[m]] = y[m];
                 ys0[row[m]] = from_d2_mc<T2>(y[m]);
             }
         }
+        sync_yf();
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < RPT; ++m)
@@ -394,27 +410,34 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
             if (cb.pub) {
                 const double hh = cb.coef[27];
                 __syncwarp();
+                double c = 0.0;
                 if (lane < 21) {
                     int s = 1, j = lane;
                     while (j >= s) {
                         j -= s;
                         ++s;
                     }
-                    cb.coef[lane] = hh * tab.a[s][j];
+                    c = hh * tab.a[s][j];
                 } else if (lane < 28) {
-                    cb.coef[lane] = hh * tab.e[lane - 21];
+                    c = hh * tab.e[lane - 21];
+                }
+                if (lane < 28) {
+                    cb.coef[lane] = c;
+                    cb.coeff[lane] = (float)c;
                 }
             }
             __syncwarp();
         };
         // One RK step of size h (coefficients in cb.coef) from (y, k1): k[1..6], ynew.
+        // MIXED keeps FP32 copies of y (yf) and y_new (yfn) so that the stage
+        // loop performs no FP64<->FP32 conversions (they run on the FP64 pipe).
         auto rk_step = [&]() {
 #pragma unroll
             for (int s = 1; s < 7; ++s) {
                 T2* ysb = (s & 1) ? ys0 : ys1;
                 T ha[6];
 #pragma unroll
-                for (int j = 0; j < 6; ++j) ha[j] = j < s ? (T)cb.coef[mc_coef_a(s, j)] : (T)0;
+                for (int j = 0; j < 6; ++j) ha[j] = j < s ? coefT(mc_coef_a(s, j)) : (T)0;
 #pragma unroll
                 for (int m = 0; m < RPT; ++m) {
                     if (!own[m]) continue;
@@ -430,9 +453,15 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
                     if (s == 6) {
                         ynew[m] = make_double2(y[m].x + (double)ax, y[m].y + (double)ay);
                         o = from_d2_mc<T2>(ynew[m]);
+                        if constexpr (MIXED) yfn[m] = o;
                     } else {
-                        o.x = (T)y[m].x + ax;
-                        o.y = (T)y[m].y + ay;
+                        if constexpr (MIXED) {
+                            o.x = yf[m].x + ax;
+                            o.y = yf[m].y + ay;
+                        } else {
+                            o.x = y[m].x + ax;
+                            o.y = y[m].y + ay;
+                        }
                     }
                     ysb[row[m]] = o;
                 }
@@ -503,7 +532,7 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
             {
                 T he[7];
 #pragma unroll
-                for (int j = 0; j < 7; ++j) he[j] = (T)cb.coef[21 + j];
+                for (int j = 0; j < 7; ++j) he[j] = coefT(21 + j);
 #pragma unroll
                 for (int m = 0; m < RPT; ++m) {
                     if (!own[m]) continue;
@@ -513,8 +542,18 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
                         ex = fma(he[j], k[j][m].x, ex);
                         ey = fma(he[j], k[j][m].y, ey);
                     }
-                    const float yx = (float)y[m].x, yy = (float)y[m].y;
-                    const float nx = (float)ynew[m].x, ny = (float)ynew[m].y;
+                    float yx, yy, nx, ny;
+                    if constexpr (MIXED) {
+                        yx = yf[m].x;
+                        yy = yf[m].y;
+                        nx = yfn[m].x;
+                        ny = yfn[m].y;
+                    } else {
+                        yx = (float)y[m].x;
+                        yy = (float)y[m].y;
+                        nx = (float)ynew[m].x;
+                        ny = (float)ynew[m].y;
+                    }
                     const float a2 = fmaxf(yx * yx + yy * yy, nx * nx + ny * ny);
                     const float sc = (float)J.atol + (float)J.rtol * sqrtf(a2);
                     const float fx = (float)ex, fy = (float)ey;
@@ -581,6 +620,7 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
 #pragma unroll
                 for (int m = 0; m < RPT; ++m) {
                     y[m] = ynew[m];
+                    yf[m] = yfn[m];
                     k[0][m] = k[6][m];
                 }
                 const int sv = cb.save;
@@ -693,6 +733,7 @@ __global__ void __launch_bounds__(MAXT) mc_traj_kernel(McJob J) {
                     ynew[m] = y[m];
                 }
             }
+            sync_yf();
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < RPT; ++m)
@@ -747,23 +788,30 @@ __global__ void mc_reduce_kernel(const double2* __restrict__ traj_expect, double
 int mc_traj_capacity() { return MC_TMAX * 4; }
 
 
-// Block sizes with their launch bounds: 4 rows per thread, the smallest
-// block that covers n.
-static int mc_block(int n) {
-    const int sizes[3] = {32, 128, 256};
-    for (int s : sizes)
-        if (4 * s >= n) return s;
-    return 0;
+// Launch shape: one row per thread up to 256 rows (so a trajectory spreads
+// over all four SM sub-partitions), then 2 or 4 rows per thread.  Each shape
+// has its own launch bounds so that the register budget keeps 6-8 CTAs of
+// 96-128 threads resident per SM.
+struct McShape {
+    int T, rpt;
+};
+static McShape mc_shape(int n) {
+    if (n <= 256) {
+        int T = (n + 31) / 32 * 32;
+        return {T < 32 ? 32 : T, 1};
+    }
+    if (n <= 512) return {256, 2};
+    if (n <= 1024) return {256, 4};
+    return {0, 0};
 }
 
-template <bool MIXED, int MAXT>
-static cudaError_t mc_launch_t(const McJob& J, cudaStream_t st) {
+template <bool MIXED, int RPT, int MAXT, int MINB>
+static cudaError_t mc_launch_t(const McJob& J, int T, cudaStream_t st) {
     using T2 = typename MPrec<MIXED>::T2;
-    const int T = MAXT;
     size_t smem = (size_t)J.n * (sizeof(double2) + 2 * sizeof(T2)) + 16 +
                   (size_t)(T / 32 + 1) * mc_red_stride(J.n_e, J.n_c) * sizeof(double) + 32;
     if (J.a_smem) smem += 16 + (size_t)J.n * sizeof(int4) + (size_t)J.a_nnz * (sizeof(T2) + 4);
-    auto kern = mc_traj_kernel<MIXED, 4, MAXT>;
+    auto kern = mc_traj_kernel<MIXED, RPT, MAXT, MINB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -782,21 +830,24 @@ static cudaError_t mc_launch_t(const McJob& J, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <bool MIXED>
+static cudaError_t mc_dispatch(const McJob& J, McShape sh, cudaStream_t st) {
+    if (sh.rpt == 1 && sh.T <= 128) return mc_launch_t<MIXED, 1, 128, 6>(J, sh.T, st);
+    if (sh.rpt == 1) return mc_launch_t<MIXED, 1, 256, 3>(J, sh.T, st);
+    if (sh.rpt == 2) return mc_launch_t<MIXED, 2, 256, 2>(J, sh.T, st);
+    return mc_launch_t<MIXED, 4, 256, 1>(J, sh.T, st);
+}
+
 cudaError_t launch_mc_traj(const McJob& J0, int precision, cudaStream_t st) {
-    const int T = mc_block(J0.n);
-    if (T == 0) return cudaErrorInvalidValue;
+    const McShape sh = mc_shape(J0.n);
+    if (sh.T == 0) return cudaErrorInvalidValue;
     // Copy A into shared memory when it fits next to the state buffers.
     McJob J = J0;
     const size_t tv = precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
     const size_t base = (size_t)J.n * (sizeof(double2) + 2 * tv) + 64 +
-                        (size_t)(T / 32 + 1) * mc_red_stride(J.n_e, J.n_c) * sizeof(double);
+                        (size_t)(sh.T / 32 + 1) * mc_red_stride(J.n_e, J.n_c) * sizeof(double);
     J.a_smem = base + 16 + (size_t)J.n * sizeof(int4) + (size_t)J.a_nnz * (tv + 4) <= 200 * 1024;
-    const bool mx = precision == QTL_MIXED;
-    switch (T) {
-        case 32: return mx ? mc_launch_t<true, 32>(J, st) : mc_launch_t<false, 32>(J, st);
-        case 128: return mx ? mc_launch_t<true, 128>(J, st) : mc_launch_t<false, 128>(J, st);
-        default: return mx ? mc_launch_t<true, 256>(J, st) : mc_launch_t<false, 256>(J, st);
-    }
+    return precision == QTL_MIXED ? mc_dispatch<true>(J, sh, st) : mc_dispatch<false>(J, sh, st);
 }
 
 cudaError_t launch_mc_reduce(const McJob& J, cudaStream_t st) {

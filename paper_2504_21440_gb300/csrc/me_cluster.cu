@@ -26,8 +26,12 @@
 // its own rows in FP64 and stores the CTA partial; the partials are added in
 // rank order at the end of the solve, so they cost no cluster barrier.
 //
-// Precision.  FP64: Liouvillian, stage sums and SpMV in FP64.  MIXED: those in
-// FP32 (complex64 operator), with y and y_new = y + h sum_j b_j k_j in FP64.
+// Precision.  FP64: Liouvillian, stage sums and SpMV in FP64.  MIXED uses the
+// increment form k_s = L y + L delta_s: the base L y is one FP64 product per
+// step (the last stage, reused as the next step's first), the O(h) stage
+// increments delta_s and their products L delta_s are FP32 (complex64
+// operator), and y_new = y + h L y + sum_j h b_j L delta_j is formed in FP64.
+// FP32 rounding then scales with |delta| ~ h|L y| instead of |L| |y|.
 #include <cooperative_groups.h>
 
 #include "internal.h"
@@ -104,7 +108,9 @@ struct MeShared {
     float wf2[ME_NW];
     float pf[2][2];                // CTA partials, double-buffered across reductions
     double we[ME_NW][2 * ME_EMAX]; // warp partials of the expectation values
-    double coef[28];               // htry * a_sj (21, packed by stage) and htry * e_j (7)
+    double coef[34];               // htry * a_sj (21, by stage), htry * e_j (7), htry * c_s (6)
+    float coeff[34];               // the same rounded to FP32 (mixed precision)
+    double hcur;                   // htry of the current attempt
     double h0, d1;
     int action, land, accept, save_idx, repeat_idx;
     int scan[ME_NW];
@@ -149,6 +155,44 @@ __device__ __forceinline__ T2 spmv_dsm(int q, const int4* __restrict__ s_seg,
     return acc;
 }
 
+// FP64 product of row q with FP64 stage inputs (the base derivative of the
+// mixed-precision increment form): structure and DSMEM addresses from the
+// shared-memory copy, FP64 values from global memory (gstart: the row's
+// first entry in the global arrays).
+__device__ __forceinline__ double2 spmv_dsm64(int q, const int4* __restrict__ s_seg,
+                                              const uint32_t* __restrict__ s_addr,
+                                              const double2* __restrict__ lv64, int gstart,
+                                              uint32_t bufoff) {
+    const int4 sg = s_seg[q];
+    const double2* v = lv64 + (gstart - sg.x);
+    double ax = 0, ay = 0, bx = 0, by = 0;
+    int p = sg.x;
+#pragma unroll 4
+    for (; p < sg.y; ++p) {
+        const double a = __ldg(&v[p].x);
+        const double2 xv = ld_dsmem(s_addr[p] + bufoff, (double2*)nullptr);
+        ax = fma(a, xv.x, ax);
+        ay = fma(a, xv.y, ay);
+    }
+#pragma unroll 4
+    for (; p < sg.z; ++p) {
+        const double b = __ldg(&v[p].y);
+        const double2 xv = ld_dsmem(s_addr[p] + bufoff, (double2*)nullptr);
+        bx = fma(-b, xv.y, bx);
+        by = fma(b, xv.x, by);
+    }
+#pragma unroll 2
+    for (; p < sg.w; ++p) {
+        const double2 a = __ldg(v + p);
+        const double2 xv = ld_dsmem(s_addr[p] + bufoff, (double2*)nullptr);
+        ax = fma(a.x, xv.x, ax);
+        ay = fma(a.x, xv.y, ay);
+        bx = fma(-a.y, xv.y, bx);
+        by = fma(a.y, xv.x, by);
+    }
+    return make_double2(ax + bx, ay + by);
+}
+
 // Exclusive prefix sum of v over the CTA; *total gets the sum.
 __device__ __forceinline__ int cta_exclusive_scan(int v, int* scratch, int* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -186,18 +230,32 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
     const RkTab& tab = RK_TABS[J.method];
     const TV* lv = MIXED ? (const TV*)J.lv32 : (const TV*)J.lv64;
 
-    // dynamic shared memory: ys[2][RPT*256], seg[RPT*256], addr[cap], v[cap]
-    T2* s_ys = (T2*)dsm;
-    const uint32_t bufoff = (uint32_t)(RPT * ME_T * sizeof(T2));
+    // dynamic shared memory: ys[2][RPT*256] (16-byte slots: an FP64 value, or
+    // an FP32 value in the slot's first half), seg[RPT*256], addr[cap], v[cap]
+    double2* s_ys = (double2*)dsm;
+    const uint32_t bufoff = (uint32_t)(RPT * ME_T * sizeof(double2));
     int4* s_seg = (int4*)(s_ys + 2 * RPT * ME_T);
     uint32_t* s_addr = (uint32_t*)(s_seg + RPT * ME_T);
     TV* s_v = (TV*)(((uintptr_t)(s_addr + J.smem_nnz) + 15) & ~(uintptr_t)15);
     const uint32_t ys_base = smem_addr(s_ys);
 
     double2 y[RPT], ynew[RPT];
+    float2 yf[RPT], yfn[RPT];  // MIXED: FP32 copies, so the stage loop converts nothing
+    // MIXED increment form: k1d = L y in FP64 (base), k[j] (j >= 1) hold the
+    // FP32 corrections c_j = L delta_j with k_j = k1d + c_j.
+    double2 k1d[RPT], k7d[RPT];
+    float2 k1f[RPT];
+    int gstart[RPT];
     T2 k[7][RPT];
     bool own[RPT];
     int row[RPT];
+    auto slot_f = [&](double2* buf, int q) -> float2* { return (float2*)(buf + q); };
+    auto coefT = [&](int i) -> T {
+        if constexpr (MIXED)
+            return sh.coeff[i];
+        else
+            return sh.coef[i];
+    };
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
         row[m] = rank + C * (tid + ME_T * m);
@@ -213,7 +271,10 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             }
         }
         ynew[m] = y[m];
-        s_ys[tid + ME_T * m] = from_d2<T2>(y[m]);
+        yf[m] = make_float2((float)y[m].x, (float)y[m].y);
+        yfn[m] = yf[m];
+        s_ys[tid + ME_T * m] = y[m];
+        gstart[m] = own[m] ? __ldg(J.seg + row[m]).x : 0;
     }
 
     // ---- this CTA's rows of the Liouvillian into shared memory ----
@@ -238,7 +299,7 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             for (int p = sg.x; p < sg.w; ++p) {
                 const int c = __ldg(J.ci + p);
                 s_addr[off + p - sg.x] =
-                    dsmem_map(ys_base + (uint32_t)((c / C) * sizeof(T2)), (uint32_t)(c % C));
+                    dsmem_map(ys_base + (uint32_t)((c / C) * sizeof(double2)), (uint32_t)(c % C));
                 s_v[off + p - sg.x] = __ldg(lv + p);
             }
             s_seg[q] = make_int4(off, off + sg.y - sg.x, off + sg.z - sg.x, off + sg.w - sg.x);
@@ -328,10 +389,18 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
         par ^= 1;
     };
 
-    // k1 = L y0, expectation values at tlist[0]
+    // k1 = L y0 (FP64 in both precisions), expectation values at tlist[0]
 #pragma unroll
-    for (int m = 0; m < RPT; ++m)
-        if (own[m]) k[0][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, 0u);
+    for (int m = 0; m < RPT; ++m) {
+        if (!own[m]) continue;
+        if constexpr (MIXED) {
+            k1d[m] = spmv_dsm64(tid + ME_T * m, s_seg, s_addr, J.lv64, gstart[m], 0u);
+            k1f[m] = make_float2((float)k1d[m].x, (float)k1d[m].y);
+            k[0][m] = k1f[m];
+        } else {
+            k[0][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, 0u);
+        }
+    }
     expect_partials(y, 0);
     states_write(0);
 
@@ -373,20 +442,34 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
         const double h0 = sh.h0;
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
-            const double2 f0 = to_d2(k[0][m]);
-            s_ys[RPT * ME_T + tid + ME_T * m] =
-                from_d2<T2>(make_double2(y[m].x + h0 * f0.x, y[m].y + h0 * f0.y));
+            if constexpr (MIXED) {
+                // increment form: f(y0 + h0 f0) - f0 = L (h0 f0)
+                *slot_f(s_ys + RPT * ME_T, tid + ME_T * m) =
+                    make_float2((float)h0 * k1f[m].x, (float)h0 * k1f[m].y);
+            } else {
+                const double2 f0 = to_d2(k[0][m]);
+                s_ys[RPT * ME_T + tid + ME_T * m] =
+                    make_double2(y[m].x + h0 * f0.x, y[m].y + h0 * f0.y);
+            }
         }
         cl.sync();
         float s2 = 0.f;
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             if (!own[m]) continue;
-            const double2 f1 = to_d2(spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff));
-            const double2 f0 = to_d2(k[0][m]);
+            float dx, dy;
+            if constexpr (MIXED) {
+                const T2 c = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff);
+                dx = (float)c.x;
+                dy = (float)c.y;
+            } else {
+                const double2 f1 = to_d2(spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff));
+                const double2 f0 = to_d2(k[0][m]);
+                dx = (float)(f1.x - f0.x);
+                dy = (float)(f1.y - f0.y);
+            }
             const float a = sqrtf((float)(y[m].x * y[m].x + y[m].y * y[m].y));
             const float sc = (float)J.atol + (float)J.rtol * a;
-            const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
             const float q = sqrtf(dx * dx + dy * dy) / sc;
             s2 += q * q;
         }
@@ -427,6 +510,7 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             sh.land = land;
             sh.action = ACT_STEP;
             sh.coef[27] = htry;  // handed to warp 0 for the coefficient products
+            sh.hcur = htry;
             return;
         }
     };
@@ -436,15 +520,30 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
         if (sh.action == ACT_STEP) {
             const double hh = sh.coef[27];
             __syncwarp();
+            double c = 0.0;
             if (lane < 21) {
                 int s = 1, j = lane;
                 while (j >= s) {
                     j -= s;
                     ++s;
                 }
-                sh.coef[lane] = hh * tab.a[s][j];
+                c = hh * tab.a[s][j];
             } else if (lane < 28) {
-                sh.coef[lane] = hh * tab.e[lane - 21];
+                c = hh * tab.e[lane - 21];
+            }
+            if (lane < 28) {
+                sh.coef[lane] = c;
+                sh.coeff[lane] = (float)c;
+            } else {
+                // htry * c_s for stages s = 1..6 (lanes 28..31 and 0..1 again)
+                const double cs = hh * tab.c[lane - 27];
+                sh.coef[lane] = cs;
+                sh.coeff[lane] = (float)cs;
+            }
+            if (lane < 2) {
+                const double cs = hh * tab.c[lane + 5];
+                sh.coef[32 + lane] = cs;
+                sh.coeff[32 + lane] = (float)cs;
             }
         }
     };
@@ -473,52 +572,104 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
 #pragma unroll
         for (int s = 1; s < 7; ++s) {
             const uint32_t off = (s & 1) ? 0u : bufoff;
-            T2* ysb = s_ys + ((s & 1) ? 0 : RPT * ME_T);
+            double2* ysb = s_ys + ((s & 1) ? 0 : RPT * ME_T);
             T ha[6];
 #pragma unroll
-            for (int j = 0; j < 6; ++j) ha[j] = j < s ? (T)sh.coef[coef_a(s, j)] : (T)0;
+            for (int j = 0; j < 6; ++j) ha[j] = j < s ? coefT(coef_a(s, j)) : (T)0;
+            if constexpr (MIXED) {
+                // increment form: stage input delta_s = h c_s k1 + sum_{j>=1} h a_sj c_j
+                // (FP32, O(h) small); its product c_s = L delta_s in FP32; the
+                // last stage forms y_new = y + h k1 + sum_j h b_j c_j in FP64 and
+                // evaluates k7 = L y_new in FP64 (the next step's base).
+                const float hc = sh.coeff[27 + s];
+                const double hcur = sh.hcur;
 #pragma unroll
-            for (int m = 0; m < RPT; ++m) {
-                T ax = 0, ay = 0;
+                for (int m = 0; m < RPT; ++m) {
+                    float ax = 0.f, ay = 0.f;
 #pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    if (j < s) {
-                        ax = fma(ha[j], k[j][m].x, ax);
-                        ay = fma(ha[j], k[j][m].y, ay);
+                    for (int j = 1; j < 6; ++j) {
+                        if (j < s) {
+                            ax = fmaf(ha[j], k[j][m].x, ax);
+                            ay = fmaf(ha[j], k[j][m].y, ay);
+                        }
+                    }
+                    if (s < 6) {
+                        ax = fmaf(hc, k1f[m].x, ax);
+                        ay = fmaf(hc, k1f[m].y, ay);
+                        *slot_f(ysb, tid + ME_T * m) = make_float2(ax, ay);
+                    } else {
+                        ynew[m] = make_double2(fma(hcur, k1d[m].x, y[m].x) + (double)ax,
+                                               fma(hcur, k1d[m].y, y[m].y) + (double)ay);
+                        yfn[m] = make_float2((float)ynew[m].x, (float)ynew[m].y);
+                        ysb[tid + ME_T * m] = ynew[m];
                     }
                 }
-                T2 o;
-                if (s == 6) {
-                    ynew[m] = make_double2(y[m].x + (double)ax, y[m].y + (double)ay);
-                    o = from_d2<T2>(ynew[m]);
-                } else {
-                    o.x = (T)y[m].x + ax;
-                    o.y = (T)y[m].y + ay;
-                }
-                ysb[tid + ME_T * m] = o;
-            }
-            cl.sync();
+                cl.sync();
 #pragma unroll
-            for (int m = 0; m < RPT; ++m)
-                if (own[m]) k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    if (s < 6) {
+                        k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+                    } else {
+                        k7d[m] = spmv_dsm64(tid + ME_T * m, s_seg, s_addr, J.lv64, gstart[m], off);
+                        k[6][m] = make_float2((float)(k7d[m].x - k1d[m].x), (float)(k7d[m].y - k1d[m].y));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    double ax = 0, ay = 0;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        if (j < s) {
+                            ax = fma((double)ha[j], (double)k[j][m].x, ax);
+                            ay = fma((double)ha[j], (double)k[j][m].y, ay);
+                        }
+                    }
+                    double2 o;
+                    if (s == 6) {
+                        ynew[m] = make_double2(y[m].x + ax, y[m].y + ay);
+                        o = ynew[m];
+                    } else {
+                        o = make_double2(y[m].x + ax, y[m].y + ay);
+                    }
+                    ysb[tid + ME_T * m] = o;
+                }
+                cl.sync();
+#pragma unroll
+                for (int m = 0; m < RPT; ++m)
+                    if (own[m]) k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+            }
         }
         // error norm: sum over own rows of (|e| / sc)^2, e = h sum_j e_j k_j
         float se = 0.f;
         {
             T he[7];
 #pragma unroll
-            for (int j = 0; j < 7; ++j) he[j] = (T)sh.coef[21 + j];
+            for (int j = 0; j < 7; ++j) he[j] = coefT(21 + j);
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
                 if (!own[m]) continue;
                 T ex = 0, ey = 0;
+                // (MIXED: k[j] are the corrections c_j; sum_j e_j = 0, so
+                // e = h sum_{j>=1} e_j c_j and the base k1 drops out)
 #pragma unroll
-                for (int j = 0; j < 7; ++j) {
+                for (int j = MIXED ? 1 : 0; j < 7; ++j) {
                     ex = fma(he[j], k[j][m].x, ex);
                     ey = fma(he[j], k[j][m].y, ey);
                 }
-                const float yx = (float)y[m].x, yy = (float)y[m].y;
-                const float nx = (float)ynew[m].x, ny = (float)ynew[m].y;
+                float yx, yy, nx, ny;
+                if constexpr (MIXED) {
+                    yx = yf[m].x;
+                    yy = yf[m].y;
+                    nx = yfn[m].x;
+                    ny = yfn[m].y;
+                } else {
+                    yx = (float)y[m].x;
+                    yy = (float)y[m].y;
+                    nx = (float)ynew[m].x;
+                    ny = (float)ynew[m].y;
+                }
                 const float a2 = fmaxf(yx * yx + yy * yy, nx * nx + ny * ny);
                 const float sc = (float)J.atol + (float)J.rtol * sqrtf(a2);
                 const float fx = (float)ex, fy = (float)ey;
@@ -564,7 +715,14 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
                 y[m] = ynew[m];
-                k[0][m] = k[6][m];
+                yf[m] = yfn[m];
+                if constexpr (MIXED) {
+                    k1d[m] = k7d[m];
+                    k1f[m] = make_float2((float)k7d[m].x, (float)k7d[m].y);
+                    k[0][m] = k1f[m];
+                } else {
+                    k[0][m] = k[6][m];
+                }
             }
             if (land) states_write(sh.save_idx);
         }
@@ -590,18 +748,32 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
     }
 }
 
+// One cluster per solve at a time.  With `next` (a zeroed device counter) the
+// clusters take jobs dynamically: rank 0 draws the next index and hands it
+// to the other CTAs over DSMEM; without it, job jb goes to cluster jb mod
+// (number of clusters).
 template <bool MIXED, int RPT>
 __global__ void __launch_bounds__(ME_T, 1) me_cluster_kernel(const MeJob* __restrict__ jobs,
-                                                              int njobs) {
+                                                              int njobs, int* next) {
     __shared__ MeShared sh;
+    __shared__ int job_slot;
     extern __shared__ __align__(16) unsigned char me_dsm[];
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
     const int cid = blockIdx.x / C, ncl = gridDim.x / C;
-    for (int jb = cid; jb < njobs; jb += ncl) {
+    int jb = cid;
+    for (;;) {
+        if (next) {
+            if (cl.block_rank() == 0 && threadIdx.x == 0) job_slot = atomicAdd(next, 1);
+            cl.sync();
+            jb = *cl.map_shared_rank(&job_slot, 0);
+            cl.sync();
+        }
+        if (jb >= njobs) break;
         const MeJob J = jobs[jb];
         me_solve<MIXED, RPT>(J, sh, cl, me_dsm);
         cl.sync();
+        if (!next) jb += ncl;
     }
 }
 
@@ -620,8 +792,8 @@ bool me_plan(int L_max, int cluster_size, int* C_out, int* rpt_out) {
 
 static size_t me_dyn_smem(int precision, int rpt, int nnz) {
     const size_t t2 = precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
-    return 2 * (size_t)rpt * ME_T * t2 + (size_t)rpt * ME_T * sizeof(int4) + (size_t)nnz * 4 + 16 +
-           (size_t)nnz * t2;
+    return 2 * (size_t)rpt * ME_T * sizeof(double2) + (size_t)rpt * ME_T * sizeof(int4) +
+           (size_t)nnz * 4 + 16 + (size_t)nnz * t2;
 }
 
 int me_smem_nnz_budget(int precision, int rpt) {
@@ -633,7 +805,7 @@ int me_smem_nnz_budget(int precision, int rpt) {
 
 template <bool MIXED, int RPT>
 static cudaError_t launch_t(const MeJob* jobs, int njobs, int C, int nclusters, int smem_nnz,
-                            cudaStream_t st) {
+                            int* next, cudaStream_t st) {
     auto kern = me_cluster_kernel<MIXED, RPT>;
     const size_t dsm = me_dyn_smem(MIXED ? QTL_MIXED : QTL_FP64, RPT, smem_nnz);
     cudaError_t e;
@@ -656,27 +828,36 @@ static cudaError_t launch_t(const MeJob* jobs, int njobs, int C, int nclusters, 
     cfg.attrs = at;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, kern, jobs, njobs);
+    return cudaLaunchKernelEx(&cfg, kern, jobs, njobs, next);
 }
 
 cudaError_t launch_me_cluster(const MeJob* jobs_dev, int njobs, int L_max, int smem_nnz,
-                              int precision, int cluster_size, cudaStream_t st) {
+                              int precision, int cluster_size, int* next, cudaStream_t st) {
     int C, rpt;
     if (!me_plan(L_max, cluster_size, &C, &rpt)) return cudaErrorInvalidValue;
     if (smem_nnz > me_smem_nnz_budget(precision, rpt)) return cudaErrorInvalidValue;
+    // clusters that can be resident at once (one CTA per SM at most, as the
+    // shared-memory footprint allows)
     int nclusters = njobs;
-    const int cap = (2 * 152) / C > 0 ? (2 * 152) / C : 1;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t dsm = me_dyn_smem(precision, rpt, smem_nnz) + sizeof(MeShared) + 1024;
+    int per_sm = (int)((228 * 1024) / dsm);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 2) per_sm = 2;
+    const int cap = (nsm * per_sm) / C > 0 ? (nsm * per_sm) / C : 1;
     if (nclusters > cap) nclusters = cap;
     if (nclusters < 1) nclusters = 1;
     const bool mixed = precision == QTL_MIXED;
     if (mixed) {
-        if (rpt == 1) return launch_t<true, 1>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
-        if (rpt == 2) return launch_t<true, 2>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
-        return launch_t<true, 4>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+        if (rpt == 1) return launch_t<true, 1>(jobs_dev, njobs, C, nclusters, smem_nnz, next, st);
+        if (rpt == 2) return launch_t<true, 2>(jobs_dev, njobs, C, nclusters, smem_nnz, next, st);
+        return launch_t<true, 4>(jobs_dev, njobs, C, nclusters, smem_nnz, next, st);
     }
-    if (rpt == 1) return launch_t<false, 1>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
-    if (rpt == 2) return launch_t<false, 2>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
-    return launch_t<false, 4>(jobs_dev, njobs, C, nclusters, smem_nnz, st);
+    if (rpt == 1) return launch_t<false, 1>(jobs_dev, njobs, C, nclusters, smem_nnz, next, st);
+    if (rpt == 2) return launch_t<false, 2>(jobs_dev, njobs, C, nclusters, smem_nnz, next, st);
+    return launch_t<false, 4>(jobs_dev, njobs, C, nclusters, smem_nnz, next, st);
 }
 
 }  // namespace qtl

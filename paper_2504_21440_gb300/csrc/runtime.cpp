@@ -466,7 +466,7 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     J.smem_nnz = (int)need;
     QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
     QTL_CUDA(cudaMemcpyAsync(jd, &J, sizeof(J), cudaMemcpyHostToDevice, stream));
-    cudaError_t e = launch_me_cluster(jd, 1, L, J.smem_nnz, opts->precision, opts->cluster_size, stream);
+    cudaError_t e = launch_me_cluster(jd, 1, L, J.smem_nnz, opts->precision, opts->cluster_size, nullptr, stream);
     if (e != cudaSuccess) {
         set_cuda_error(e);
         cudaFreeAsync(scratch, stream);
@@ -474,6 +474,246 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     }
     QTL_CUDA(cudaFreeAsync(scratch, stream));
     return QTL_OK;
+}
+
+// ---------------------------------------------------------------- batches
+namespace {
+
+// Streams forked from the caller's stream for concurrent launch plans
+// (created once per device).
+std::mutex g_fork_mu;
+std::vector<cudaStream_t> g_fork[64];
+
+qtl_status fork_streams(int k, cudaStream_t** out) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return QTL_EINVAL;
+    std::lock_guard<std::mutex> lk(g_fork_mu);
+    while ((int)g_fork[dev].size() < k) {
+        cudaStream_t s;
+        QTL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        g_fork[dev].push_back(s);
+    }
+    *out = g_fork[dev].data();
+    return QTL_OK;
+}
+
+// Launch plan of one system in a batch: cluster size from its own size.
+void batch_plan(int L, int* C, int* rpt) {
+    int c = 1;
+    while (c < 16 && (int64_t)c * 1024 < L) c *= 2;
+    me_plan(L, c, C, rpt);
+}
+
+int64_t cta_nnz_max(const System& s, int C) {
+    const int L = s.n * s.n;
+    std::vector<int64_t> per(C, 0);
+    for (int r = 0; r < L; ++r) per[r % C] += s.L_rp[r + 1] - s.L_rp[r];
+    return *std::max_element(per.begin(), per.end());
+}
+
+}  // namespace
+
+extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_t nb,
+                                              const qtl_c128* const* state0_dev, const int32_t* is_ket,
+                                              const double* tlist_dev, int32_t nt, const qtl_opts* opts,
+                                              qtl_c128* const* expect_dev, qtl_device_info* info_dev) {
+    if (!systems || nb < 1 || !state0_dev || !is_ket || !tlist_dev || nt < 1 || !expect_dev || !info_dev)
+        return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    struct Plan {
+        int C, rpt;
+        int64_t need;
+    };
+    std::vector<Plan> plan(nb);
+    for (int b = 0; b < nb; ++b) {
+        if (!systems[b] || !state0_dev[b] || (systems[b]->s.n_e > 0 && !expect_dev[b])) return QTL_EINVAL;
+        System& s = systems[b]->s;
+        if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+        const int L = s.n * s.n;
+        batch_plan(L, &plan[b].C, &plan[b].rpt);
+        plan[b].need = cta_nnz_max(s, plan[b].C);
+        if (plan[b].need > me_smem_nnz_budget(opts->precision, plan[b].rpt)) return QTL_ETOOBIG;
+    }
+    // buckets of equal plans, jobs ordered by decreasing Liouvillian size
+    std::vector<std::pair<int, int>> keys;
+    for (int b = 0; b < nb; ++b) {
+        std::pair<int, int> k(plan[b].C, plan[b].rpt);
+        if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+    }
+    const int nk = (int)keys.size();
+    std::vector<std::vector<int>> bucket(nk);
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < nk; ++k)
+            if (keys[k] == std::make_pair(plan[b].C, plan[b].rpt)) bucket[k].push_back(b);
+    for (auto& v : bucket)
+        std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+            return systems[x]->s.dL.nnz > systems[y]->s.dL.nnz;
+        });
+    // scratch: jobs (bucket order), per-job expectation partials, counters
+    std::vector<size_t> ep_off(nb);
+    size_t off = ((size_t)nb * sizeof(MeJob) + 255) & ~(size_t)255;
+    const size_t cnt_off = off;
+    off += ((size_t)nk * sizeof(int) + 255) & ~(size_t)255;
+    for (int b = 0; b < nb; ++b) {
+        ep_off[b] = off;
+        const int ne = systems[b]->s.n_e > 0 ? systems[b]->s.n_e : 1;
+        off += (((size_t)nt * plan[b].C * 2 * ne * sizeof(double)) + 255) & ~(size_t)255;
+    }
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    char* scratch = nullptr;
+    QTL_CUDA(cudaMallocAsync((void**)&scratch, off, stream));
+    std::vector<MeJob> jobs(nb);
+    std::vector<int> first(nk + 1, 0);
+    int q = 0;
+    for (int k = 0; k < nk; ++k) {
+        first[k] = q;
+        for (int b : bucket[k]) {
+            System& s = systems[b]->s;
+            MeJob& J = jobs[q++];
+            std::memset(&J, 0, sizeof(J));
+            J.n = s.n;
+            J.L = s.n * s.n;
+            J.seg = s.dL.seg;
+            J.ci = s.dL.ci;
+            J.lv64 = s.dL.v64;
+            J.lv32 = s.dL.v32;
+            J.n_e = s.n_e;
+            J.ew = s.ew;
+            J.tlist = tlist_dev;
+            J.nt = nt;
+            J.state0 = (const double2*)state0_dev[b];
+            J.is_ket = is_ket[b] ? 1 : 0;
+            J.epart = (double*)(scratch + ep_off[b]);
+            J.expect = (double2*)expect_dev[b];
+            J.states = nullptr;
+            J.info = info_dev + b;
+            J.rtol = opts->rtol;
+            J.atol = opts->atol;
+            J.dt0 = opts->dt0;
+            J.dt_min = opts->dt_min;
+            J.dt_fixed = opts->dt_fixed;
+            J.max_steps = opts->max_steps;
+            J.fixed = opts->fixed_step ? 1 : 0;
+            J.method = opts->method;
+            J.smem_nnz = 0;
+        }
+    }
+    first[nk] = q;
+    for (int k = 0; k < nk; ++k) {
+        int64_t need = 0;
+        for (int b : bucket[k]) need = std::max(need, plan[b].need);
+        for (int j = first[k]; j < first[k + 1]; ++j) jobs[j].smem_nnz = (int)need;
+    }
+    MeJob* jd = (MeJob*)scratch;
+    int* counters = (int*)(scratch + cnt_off);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(info_dev, 0, (size_t)nb * sizeof(qtl_device_info), stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(counters, 0, (size_t)nk * sizeof(int), stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(jd, jobs.data(), (size_t)nb * sizeof(MeJob), cudaMemcpyHostToDevice,
+                             stream)) != cudaSuccess) {
+        set_cuda_error(e);
+        cudaFreeAsync(scratch, stream);
+        return QTL_ECUDA;
+    }
+    cudaStream_t* fs = nullptr;
+    if (nk > 1 && (st = fork_streams(nk, &fs)) != QTL_OK) {
+        cudaFreeAsync(scratch, stream);
+        return st;
+    }
+    cudaEvent_t fork_ev = nullptr;
+    if (nk > 1) {
+        cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming);
+        cudaEventRecord(fork_ev, stream);
+    }
+    e = cudaSuccess;
+    for (int k = 0; k < nk && e == cudaSuccess; ++k) {
+        cudaStream_t sk = nk > 1 ? fs[k] : stream;
+        if (nk > 1) cudaStreamWaitEvent(sk, fork_ev, 0);
+        int Lmax = 0;
+        for (int b : bucket[k]) Lmax = std::max(Lmax, systems[b]->s.n * systems[b]->s.n);
+        e = launch_me_cluster(jd + first[k], first[k + 1] - first[k], Lmax, jobs[first[k]].smem_nnz,
+                              opts->precision, keys[k].first, counters + k, sk);
+        if (nk > 1) {
+            cudaEvent_t done;
+            cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+            cudaEventRecord(done, sk);
+            cudaStreamWaitEvent(stream, done, 0);
+            cudaEventDestroy(done);
+        }
+    }
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    cudaFreeAsync(scratch, stream);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return QTL_ECUDA;
+    }
+    return QTL_OK;
+}
+
+extern "C" qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb,
+                                        const qtl_c128* const* state0, const int32_t* is_ket,
+                                        const double* tlist, int32_t nt, const qtl_opts* opts,
+                                        qtl_c128* const* expect_out, qtl_stats* stats) {
+    if (!systems || nb < 1 || !state0 || !is_ket || !expect_out) return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    std::vector<size_t> s_off(nb), e_off(nb), s_len(nb), e_len(nb);
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off = (off + b + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t tl_off = take((size_t)nt * 8);
+    const size_t info_off = take((size_t)nb * sizeof(qtl_device_info));
+    for (int b = 0; b < nb; ++b) {
+        if (!systems[b] || !state0[b]) return QTL_EINVAL;
+        const System& s = systems[b]->s;
+        s_len[b] = (is_ket[b] ? (size_t)s.n : (size_t)s.n * s.n) * 16;
+        for (size_t i = 0; i < s_len[b] / 16; ++i)
+            if (!finite_c(state0[b][i])) return QTL_EINVAL;
+        e_len[b] = (size_t)s.n_e * nt * 16;
+        s_off[b] = take(s_len[b]);
+        e_off[b] = take(e_len[b]);
+    }
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    char* buf = nullptr;
+    QTL_CUDA(cudaMallocAsync((void**)&buf, off, stream));
+    std::vector<const qtl_c128*> sd(nb);
+    std::vector<qtl_c128*> ed(nb);
+    QTL_CUDA(cudaMemcpyAsync(buf + tl_off, tlist, (size_t)nt * 8, cudaMemcpyHostToDevice, stream));
+    for (int b = 0; b < nb; ++b) {
+        sd[b] = (const qtl_c128*)(buf + s_off[b]);
+        ed[b] = (qtl_c128*)(buf + e_off[b]);
+        QTL_CUDA(cudaMemcpyAsync(buf + s_off[b], state0[b], s_len[b], cudaMemcpyHostToDevice, stream));
+    }
+    st = qtl_mesolve_batch_async(systems, nb, sd.data(), is_ket, (const double*)(buf + tl_off), nt, opts,
+                                 ed.data(), (qtl_device_info*)(buf + info_off));
+    if (st != QTL_OK) {
+        cudaFreeAsync(buf, stream);
+        return st;
+    }
+    std::vector<qtl_device_info> info(nb);
+    for (int b = 0; b < nb; ++b)
+        if (e_len[b]) QTL_CUDA(cudaMemcpyAsync(expect_out[b], buf + e_off[b], e_len[b], cudaMemcpyDeviceToHost, stream));
+    QTL_CUDA(cudaMemcpyAsync(info.data(), buf + info_off, (size_t)nb * sizeof(qtl_device_info),
+                             cudaMemcpyDeviceToHost, stream));
+    QTL_CUDA(cudaFreeAsync(buf, stream));
+    QTL_CUDA(cudaStreamSynchronize(stream));
+    qtl_status first_bad = QTL_OK;
+    for (int b = 0; b < nb; ++b) {
+        if (stats) {
+            stats[b].steps_acc = info[b].steps_acc;
+            stats[b].steps_rej = info[b].steps_rej;
+            stats[b].rhs_evals = info[b].rhs_evals;
+            stats[b].jumps = info[b].jumps;
+        }
+        if (first_bad == QTL_OK && info[b].status != QTL_OK) first_bad = (qtl_status)info[b].status;
+    }
+    return first_bad;
 }
 
 qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket, const double* tlist,

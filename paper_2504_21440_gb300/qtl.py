@@ -88,6 +88,11 @@ def load():
     lib.qtl_mcsolve_async.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.c_int64,
                                       C.POINTER(Opts), P, P, P]
     lib.qtl_mcsolve_async.restype = C.c_int
+    lib.qtl_mesolve_batch.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P,
+                                      C.POINTER(Stats)]
+    lib.qtl_mesolve_batch.restype = C.c_int
+    lib.qtl_mesolve_batch_async.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P]
+    lib.qtl_mesolve_batch_async.restype = C.c_int
     lib.qtl_mcsolve_noalloc.argtypes = [C.c_int32, P, P, P, C.c_int64, C.c_int32, P, P, P,
                                         C.c_int32, P, P, P, P, P, C.c_int32, C.c_int32,
                                         C.c_uint64, C.c_int64, C.POINTER(Opts), P, P]
@@ -247,6 +252,47 @@ def mcsolve_async(sys, psi0_dev, tlist_dev, ntraj, seed, opts, expect_dev, traj_
                                     int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
                                     int(traj_offset), C.byref(opts), _ptr(expect_dev),
                                     _ptr(traj_expect_dev), _ptr(info_dev)), "qtl_mcsolve_async")
+
+
+def batch_cluster_size(n):
+    """Cluster size the batch entry points give a system of dimension n."""
+    c = 1
+    while c < 16 and c * 1024 < n * n:
+        c *= 2
+    return c
+
+
+def mesolve_batch(handles, n_es, states0, tlist, opts):
+    """qtl_mesolve_batch with host arrays: one expectation array [n_e, nt] and
+    one stats dict per system."""
+    lib = load()
+    nb = len(handles)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt = len(tl)
+    st0 = [np.ascontiguousarray(x, dtype=np.complex128) for x in states0]
+    st0 = [x if x.ndim == 1 else np.ascontiguousarray(x.reshape(-1, order="F")) for x in st0]
+    is_ket = (C.c_int32 * nb)(*[1 if np.ndim(x) == 1 and len(x) == system_dim(h) else 0
+                                 for x, h in zip(st0, handles)])
+    outs = [np.zeros((max(ne, 1), nt), dtype=np.complex128) for ne in n_es]
+    harr = (C.c_void_p * nb)(*[h.value if hasattr(h, "value") else h for h in handles])
+    sarr = (C.c_void_p * nb)(*[x.ctypes.data for x in st0])
+    earr = (C.c_void_p * nb)(*[o.ctypes.data for o in outs])
+    stats = (Stats * nb)()
+    _check(lib.qtl_mesolve_batch(harr, nb, sarr, is_ket, _ptr(tl), nt, C.byref(opts), earr, stats),
+           "qtl_mesolve_batch")
+    return [dict(expect=o[:ne], stats=stats[b].as_dict()) for b, (o, ne) in enumerate(zip(outs, n_es))]
+
+
+def mesolve_batch_async(handles, states_dev, is_ket, tlist_dev, opts, expects_dev, info_dev):
+    """qtl_mesolve_batch_async: device tensors, enqueued on opts.cuda_stream."""
+    nb = len(handles)
+    harr = (C.c_void_p * nb)(*[h.value if hasattr(h, "value") else h for h in handles])
+    sarr = (C.c_void_p * nb)(*[x.data_ptr() for x in states_dev])
+    karr = (C.c_int32 * nb)(*[int(k) for k in is_ket])
+    earr = (C.c_void_p * nb)(*[x.data_ptr() for x in expects_dev])
+    _check(load().qtl_mesolve_batch_async(harr, nb, sarr, karr, _ptr(tlist_dev), int(tlist_dev.numel()),
+                                          C.byref(opts), earr, _ptr(info_dev)), "qtl_mesolve_batch_async")
+    return (harr, sarr, karr, earr)
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
