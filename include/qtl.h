@@ -83,7 +83,14 @@ enum { QTL_FP64 = 0, QTL_MIXED = 1 };
  *   max_steps     attempted steps per solve (per trajectory for mcsolve)
  *   fixed_step    1: every step has size min(dt_fixed, time to the next
  *                 tlist point) and is accepted without error control
- *   cuda_stream   cudaStream_t to run on; NULL = the legacy default stream */
+ *   cuda_stream   cudaStream_t to run on; NULL = the legacy default stream
+ *   engine        mesolve kernel: QTL_ENGINE_AUTO (cluster kernel when n*n and
+ *                 the Liouvillian fit one 16-CTA cluster, else the grid
+ *                 kernel), QTL_ENGINE_CLUSTER (CSR Liouvillian in one thread-
+ *                 block cluster; QTL_ETOOBIG if it does not fit) or
+ *                 QTL_ENGINE_GRID (product form A rho + rho B + sum C rho C^dag
+ *                 over a cooperative grid; no Liouvillian is formed) */
+enum { QTL_ENGINE_AUTO = 0, QTL_ENGINE_CLUSTER = 1, QTL_ENGINE_GRID = 2 };
 typedef struct {
     int32_t method;
     int32_t precision;
@@ -96,6 +103,8 @@ typedef struct {
     int32_t cluster_size; /* mesolve: CTAs per solve (0 = automatic, 1..16) */
     double dt_fixed;
     void* cuda_stream;
+    int32_t engine;
+    int32_t reserved;
 } qtl_opts;
 
 /* Counters of one solve (summed over trajectories for mcsolve). */
@@ -157,8 +166,9 @@ int64_t qtl_system_nnz(const qtl_system* sys, int32_t which);
  *   expect_out[n_e*nt] (row k = e_op k): Tr(O_k rho(tlist[t])); may be NULL if n_e = 0.
  *   states_out NULL, or [nt*n*n]: vec(rho(tlist[t])) for each t.
  *   stats      NULL or filled.
- * Host pointers; returns when done.  QTL_ETOOBIG when n*n exceeds the
- * cluster kernel's capacity (65536 entries). */
+ * Host pointers; returns when done.  The cluster kernel takes n*n up to
+ * 16384 (and a Liouvillian whose rows fit each CTA's shared memory); larger
+ * problems run on the grid kernel (opts->engine). */
 qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket,
                        const double* tlist, int32_t nt, const qtl_opts* opts,
                        qtl_c128* expect_out, qtl_c128* states_out, qtl_stats* stats);

@@ -43,7 +43,8 @@ struct System {
     Csr A;                // -i H - 1/2 sum C^dag C
     Csr Bt;               // (i H - 1/2 sum C^dag C)^T
     // device
-    DevCsr dA;            // mcsolve RHS
+    DevCsr dA;            // mcsolve RHS; left factor of the product-form RHS
+    DevCsr dBt;           // B^T (B = i H - 1/2 sum C^dag C): right factor of the product form
     DevCsr dC;            // all collapse operators stacked: rows k*n .. k*n+n-1
     DevCsr dO;            // all observables stacked: rows k*n .. k*n+n-1
     DevCsr dL;            // Liouvillian (built lazily)
@@ -74,6 +75,46 @@ struct MeJob {
     int fixed;
     int method;
     int smem_nnz;         // per-CTA shared-memory capacity for Liouvillian entries
+};
+
+// Large-rho mesolve (one cooperative grid per solve, product-form RHS).
+struct MgJob {
+    int n;
+    long long L;
+    const int4* aseg;     // A, segmented rows
+    const int32_t* aci;
+    const double2* av64;
+    const float2* av32;
+    const int4* bseg;     // B^T, segmented rows
+    const int32_t* bci;
+    const double2* bv64;
+    const float2* bv32;
+    int n_c;
+    const int32_t* crp;   // collapse operators stacked row-wise (plain CSR)
+    const int32_t* cci;
+    const double2* cv64;
+    const float2* cv32;
+    int n_e;
+    const int32_t* orp;   // observables stacked row-wise (plain CSR)
+    const int32_t* oci;
+    const double2* ov;
+    const double* tlist;
+    int nt;
+    const double2* state0;
+    int is_ket;
+    double2* y0buf;       // scratch [L] FP64 state (two alternating buffers: y, y_new)
+    double2* y1buf;
+    void* k;              // scratch [7][L] stage derivatives (FP64 or FP32)
+    void* ys;             // scratch [2][L] stage inputs (FP64 or FP32)
+    float* errpart;       // scratch [grid] error partials
+    double* epart;        // scratch [nt][grid][2 n_e] expectation partials
+    double2* expect;      // [n_e*nt]
+    double2* states;      // [nt*L] or null
+    qtl_device_info* info;
+    double rtol, atol, dt0, dt_min, dt_fixed;
+    long long max_steps;
+    int fixed;
+    int method;
 };
 
 struct McJob {
@@ -119,7 +160,9 @@ cudaError_t launch_info_init(qtl_device_info* info, cudaStream_t st);
 
 qtl_status validate_opts(const qtl_opts* o);
 
-int me_cluster_capacity();        // max L handled by the cluster kernel
+int me_cluster_capacity();
+cudaError_t launch_me_grid(const MgJob& J, int precision, cudaStream_t st, int* grid_out);
+int me_grid_blocks(int precision);        // max L handled by the cluster kernel
 int mc_traj_capacity();           // max n handled by the trajectory kernel
 
 void count_launch(int k = 1);

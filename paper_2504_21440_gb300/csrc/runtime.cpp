@@ -294,6 +294,7 @@ static qtl_status check_opts(const qtl_opts* o) {
     }
     if (!(o->dt0 >= 0.0) || !(o->dt_min >= 0.0) || o->max_steps <= 0) return QTL_EINVAL;
     if (o->cluster_size < 0 || o->cluster_size > 16) return QTL_EINVAL;
+    if (o->engine < QTL_ENGINE_AUTO || o->engine > QTL_ENGINE_GRID) return QTL_EINVAL;
     return QTL_OK;
 }
 
@@ -304,6 +305,88 @@ static qtl_status check_tlist_host(const double* tl, int nt) {
     for (int i = 0; i < nt; ++i) {
         if (!std::isfinite(tl[i])) return QTL_EINVAL;
         if (i > 0 && tl[i] < tl[i - 1]) return QTL_EINVAL;
+    }
+    return QTL_OK;
+}
+
+int64_t cta_nnz_max_of(const System& s, int C) {
+    const int L = s.n * s.n;
+    std::vector<int64_t> per(C, 0);
+    for (int r = 0; r < L; ++r) per[r % C] += s.L_rp[r + 1] - s.L_rp[r];
+    return *std::max_element(per.begin(), per.end());
+}
+
+// mesolve on the cooperative grid kernel (product form, no Liouvillian).
+qtl_status mesolve_grid(System& s, const qtl_c128* state0_dev, int32_t is_ket, const double* tlist_dev,
+                        int32_t nt, const qtl_opts* opts, qtl_c128* expect_dev, qtl_c128* states_dev,
+                        qtl_device_info* info_dev) {
+    const size_t L = (size_t)s.n * s.n;
+    if (L > (size_t)INT32_MAX) return QTL_ETOOBIG;
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    const int grid = me_grid_blocks(opts->precision);
+    const size_t t2 = opts->precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
+    const int ne = s.n_e > 0 ? s.n_e : 1;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_y = up(L * 16), b_k = up(7 * L * t2), b_ys = up(2 * L * t2);
+    const size_t b_err = up(3 * (size_t)grid * sizeof(float));
+    const size_t b_ep = up((size_t)nt * grid * 2 * ne * sizeof(double));
+    char* scratch = nullptr;
+    QTL_CUDA(cudaMallocAsync((void**)&scratch, 2 * b_y + b_k + b_ys + b_err + b_ep, stream));
+    MgJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.n = s.n;
+    J.L = (long long)L;
+    J.aseg = s.dA.seg;
+    J.aci = s.dA.ci;
+    J.av64 = s.dA.v64;
+    J.av32 = s.dA.v32;
+    J.bseg = s.dBt.seg;
+    J.bci = s.dBt.ci;
+    J.bv64 = s.dBt.v64;
+    J.bv32 = s.dBt.v32;
+    J.n_c = s.n_c;
+    J.crp = s.dC.rp;
+    J.cci = s.dC.ci;
+    J.cv64 = s.dC.v64;
+    J.cv32 = s.dC.v32;
+    J.n_e = s.n_e;
+    J.orp = s.dO.rp;
+    J.oci = s.dO.ci;
+    J.ov = s.dO.v64;
+    J.tlist = tlist_dev;
+    J.nt = nt;
+    J.state0 = (const double2*)state0_dev;
+    J.is_ket = is_ket ? 1 : 0;
+    size_t off = 0;
+    J.y0buf = (double2*)(scratch + off);
+    off += b_y;
+    J.y1buf = (double2*)(scratch + off);
+    off += b_y;
+    J.k = scratch + off;
+    off += b_k;
+    J.ys = scratch + off;
+    off += b_ys;
+    J.errpart = (float*)(scratch + off);
+    off += b_err;
+    J.epart = (double*)(scratch + off);
+    J.expect = (double2*)expect_dev;
+    J.states = (double2*)states_dev;
+    J.info = info_dev;
+    J.rtol = opts->rtol;
+    J.atol = opts->atol;
+    J.dt0 = opts->dt0;
+    J.dt_min = opts->dt_min;
+    J.dt_fixed = opts->dt_fixed;
+    J.max_steps = opts->max_steps;
+    J.fixed = opts->fixed_step ? 1 : 0;
+    J.method = opts->method;
+    QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
+    int g = grid;
+    cudaError_t e = launch_me_grid(J, opts->precision, stream, &g);
+    cudaFreeAsync(scratch, stream);
+    if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return QTL_ECUDA;
     }
     return QTL_OK;
 }
@@ -328,6 +411,8 @@ void qtl_opts_default(qtl_opts* o) {
     o->cluster_size = 0;
     o->dt_fixed = 0.0;
     o->cuda_stream = nullptr;
+    o->engine = QTL_ENGINE_AUTO;
+    o->reserved = 0;
 }
 
 const char* qtl_strerror(qtl_status s) {
@@ -352,6 +437,7 @@ void qtl_system_free(qtl_system* sys) {
     if (!sys) return;
     System& s = sys->s;
     free_csr(s.dA);
+    free_csr(s.dBt);
     free_csr(s.dC);
     free_csr(s.dO);
     free_csr(s.dL);
@@ -390,7 +476,8 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c, 
     Csr Cs, Os;
     stack(s.C, s.n, Cs);
     stack(s.O, s.n, Os);
-    if ((st = upload_csr(s.A, s.dA)) != QTL_OK || (st = upload_csr(Cs, s.dC)) != QTL_OK ||
+    if ((st = upload_csr(s.A, s.dA)) != QTL_OK || (st = upload_csr(s.Bt, s.dBt)) != QTL_OK ||
+        (st = upload_csr(Cs, s.dC)) != QTL_OK ||
         (st = upload_csr(Os, s.dO)) != QTL_OK) {
         qtl_system_free(sys);
         return st;
@@ -421,6 +508,20 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     qtl_status st = check_opts(opts);
     if (st != QTL_OK) return st;
     System& s = sys->s;
+    {
+        // engine: the cluster kernel when the problem fits one cluster
+        const int64_t L64 = (int64_t)s.n * s.n;
+        bool grid = opts->engine == QTL_ENGINE_GRID ||
+                    (opts->engine == QTL_ENGINE_AUTO && L64 > me_cluster_capacity());
+        if (!grid && opts->engine == QTL_ENGINE_AUTO) {
+            if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+            int C = 0, rpt = 0;
+            me_plan((int)L64, opts->cluster_size, &C, &rpt);
+            grid = cta_nnz_max_of(s, C) > me_smem_nnz_budget(opts->precision, rpt);
+        }
+        if (grid)
+            return mesolve_grid(s, state0_dev, is_ket, tlist_dev, nt, opts, expect_dev, states_dev, info_dev);
+    }
     if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     const int L = s.n * s.n;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libqtl.so")
 QTL_OK, QTL_EINVAL, QTL_ENOMEM, QTL_ESTEP, QTL_ECUDA, QTL_ECANCEL, QTL_EBUSY, QTL_ETOOBIG = range(8)
 METHODS = {"dp5": 0, "tsit5": 1}
 PRECISIONS = {"fp64": 0, "mixed": 1}
+ENGINES = {"auto": 0, "cluster": 1, "grid": 2}
 
 
 class QtlError(RuntimeError):
@@ -35,7 +36,8 @@ class Opts(C.Structure):
     _fields_ = [("method", C.c_int32), ("precision", C.c_int32), ("rtol", C.c_double),
                 ("atol", C.c_double), ("dt0", C.c_double), ("dt_min", C.c_double),
                 ("max_steps", C.c_int64), ("fixed_step", C.c_int32), ("cluster_size", C.c_int32),
-                ("dt_fixed", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("dt_fixed", C.c_double), ("cuda_stream", C.c_void_p), ("engine", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -126,7 +128,7 @@ def opts_default():
 
 
 def make_opts(method="tsit5", precision="fp64", rtol=1e-8, atol=1e-10, dt0=0.0, dt_min=0.0,
-              max_steps=10_000_000, fixed_dt=None, cluster_size=0, stream=None):
+              max_steps=10_000_000, fixed_dt=None, cluster_size=0, stream=None, engine="auto"):
     o = opts_default()
     o.method = METHODS[method]
     o.precision = PRECISIONS[precision]
@@ -136,6 +138,7 @@ def make_opts(method="tsit5", precision="fp64", rtol=1e-8, atol=1e-10, dt0=0.0, 
     o.dt_fixed = float(fixed_dt) if fixed_dt is not None else 0.0
     o.cluster_size = int(cluster_size)
     o.cuda_stream = stream
+    o.engine = ENGINES[engine]
     return o
 
 
