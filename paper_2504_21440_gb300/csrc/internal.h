@@ -50,6 +50,9 @@ struct System {
     DevCsr dL;            // Liouvillian (built lazily)
     std::vector<int32_t> L_rp;  // host copy of its row pointers (shared-memory sizing)
     double2* ew = nullptr;      // [n*n][n_e] trace weights (built with the Liouvillian)
+    int32_t* cmap = nullptr;    // [n_c][n] column of C_c's entry in row i, -1 if none
+    double2* cval64 = nullptr;  // [n_c][n] its value (only when every row has <= 1 entry)
+    float2* cval32 = nullptr;
     int device = 0;
 };
 
@@ -94,6 +97,9 @@ struct MgJob {
     const int32_t* cci;
     const double2* cv64;
     const float2* cv32;
+    const int32_t* cmap;  // monomial collapse operators: [n_c][n] column map (or null)
+    const double2* cmv64;
+    const float2* cmv32;
     int n_e;
     const int32_t* orp;   // observables stacked row-wise (plain CSR)
     const int32_t* oci;

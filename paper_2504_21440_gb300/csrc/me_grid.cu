@@ -86,7 +86,7 @@ __device__ __forceinline__ V g_warp_sum(V v) {
 template <class T2, class TV>
 __device__ __forceinline__ T2 rhs_entry(const MgJob& J, const T2* __restrict__ Y, int a, int b,
                                         const TV* __restrict__ av, const TV* __restrict__ bv,
-                                        const TV* __restrict__ cv) {
+                                        const TV* __restrict__ cv, const void* cmvp) {
     using T = decltype(T2::x);
     const size_t n = (size_t)J.n;
     T ax = 0, ay = 0, bx = 0, by = 0;
@@ -142,7 +142,25 @@ __device__ __forceinline__ T2 rhs_entry(const MgJob& J, const T2* __restrict__ Y
             by = fma(v.y, x.x, by);
         }
     }
-    // C rho C^dag: sum over rows a and b of each C_k
+    // C rho C^dag
+    if (J.cmap) {
+        // every C_k has at most one entry per row: (C Y C^dag)_ab =
+        // c(a) conj(c(b)) Y[m(a), m(b)], m the column map
+        const TV* cmv = (const TV*)cmvp;
+        for (int c = 0; c < J.n_c; ++c) {
+            const int ma = __ldg(J.cmap + (size_t)c * n + a);
+            const int mb = __ldg(J.cmap + (size_t)c * n + b);
+            if (ma >= 0 && mb >= 0) {
+                const TV u = __ldg(cmv + (size_t)c * n + a), w = __ldg(cmv + (size_t)c * n + b);
+                const T gx = u.x * w.x + u.y * w.y, gy = u.y * w.x - u.x * w.y;
+                const T2 x = __ldcg(Y + (size_t)ma + n * (size_t)mb);
+                ax = fma(gx, x.x, ax);
+                ay = fma(gx, x.y, ay);
+                bx = fma(-gy, x.y, bx);
+                by = fma(gy, x.x, by);
+            }
+        }
+    } else
     for (int c = 0; c < J.n_c; ++c) {
         const int ra = c * J.n + a, rb = c * J.n + b;
         const int pa0 = __ldg(J.crp + ra), pa1 = __ldg(J.crp + ra + 1);
@@ -166,6 +184,139 @@ __device__ __forceinline__ T2 rhs_entry(const MgJob& J, const T2* __restrict__ Y
     r.x = ax + bx;
     r.y = ay + by;
     return r;
+}
+
+// The same right-hand side for four entries (a, b[0..3]) of one row a: the
+// row of A and the collapse maps of row a are loaded once and their gathers
+// for the four columns are independent, so they overlap.
+template <class T2, class TV>
+__device__ __forceinline__ void rhs_row4(const MgJob& J, const T2* __restrict__ Y, int a,
+                                         const int* b, T2* out, const TV* __restrict__ av,
+                                         const TV* __restrict__ bv, const TV* __restrict__ cv,
+                                         const void* cmvp) {
+    using T = decltype(T2::x);
+    const size_t n = (size_t)J.n;
+    T ax[4], ay[4], bx[4], by[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ax[k] = ay[k] = bx[k] = by[k] = 0;
+    // A rho: one pass over row a of A for all four columns
+    {
+        const int4 sg = __ldg(J.aseg + a);
+        int p = sg.x;
+        for (; p < sg.y; ++p) {
+            const T v = __ldg(&av[p].x);
+            const size_t c = (size_t)__ldg(J.aci + p);
+            T2 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = __ldcg(Y + c + n * (size_t)b[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ax[k] = fma(v, x[k].x, ax[k]);
+                ay[k] = fma(v, x[k].y, ay[k]);
+            }
+        }
+        for (; p < sg.z; ++p) {
+            const T v = __ldg(&av[p].y);
+            const size_t c = (size_t)__ldg(J.aci + p);
+            T2 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = __ldcg(Y + c + n * (size_t)b[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                bx[k] = fma(-v, x[k].y, bx[k]);
+                by[k] = fma(v, x[k].x, by[k]);
+            }
+        }
+        for (; p < sg.w; ++p) {
+            const TV v = __ldg(av + p);
+            const size_t c = (size_t)__ldg(J.aci + p);
+            T2 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = __ldcg(Y + c + n * (size_t)b[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ax[k] = fma(v.x, x[k].x, ax[k]);
+                ay[k] = fma(v.x, x[k].y, ay[k]);
+                bx[k] = fma(-v.y, x[k].y, bx[k]);
+                by[k] = fma(v.y, x[k].x, by[k]);
+            }
+        }
+    }
+    // rho B: row b of B^T for each column (the same for a whole warp)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int4 sg = __ldg(J.bseg + b[k]);
+        const T2* rowa = Y + a;
+        int p = sg.x;
+        for (; p < sg.y; ++p) {
+            const T v = __ldg(&bv[p].x);
+            const T2 x = __ldcg(rowa + n * (size_t)__ldg(J.bci + p));
+            ax[k] = fma(v, x.x, ax[k]);
+            ay[k] = fma(v, x.y, ay[k]);
+        }
+        for (; p < sg.z; ++p) {
+            const T v = __ldg(&bv[p].y);
+            const T2 x = __ldcg(rowa + n * (size_t)__ldg(J.bci + p));
+            bx[k] = fma(-v, x.y, bx[k]);
+            by[k] = fma(v, x.x, by[k]);
+        }
+        for (; p < sg.w; ++p) {
+            const TV v = __ldg(bv + p);
+            const T2 x = __ldcg(rowa + n * (size_t)__ldg(J.bci + p));
+            ax[k] = fma(v.x, x.x, ax[k]);
+            ay[k] = fma(v.x, x.y, ay[k]);
+            bx[k] = fma(-v.y, x.y, bx[k]);
+            by[k] = fma(v.y, x.x, by[k]);
+        }
+    }
+    // C rho C^dag
+    if (J.cmap) {
+        const TV* cmv = (const TV*)cmvp;
+        for (int c = 0; c < J.n_c; ++c) {
+            const int ma = __ldg(J.cmap + (size_t)c * n + a);
+            if (ma < 0) continue;
+            const TV u = __ldg(cmv + (size_t)c * n + a);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int mb = __ldg(J.cmap + (size_t)c * n + b[k]);
+                if (mb < 0) continue;
+                const TV w = __ldg(cmv + (size_t)c * n + b[k]);
+                const T gx = u.x * w.x + u.y * w.y, gy = u.y * w.x - u.x * w.y;
+                const T2 x = __ldcg(Y + (size_t)ma + n * (size_t)mb);
+                ax[k] = fma(gx, x.x, ax[k]);
+                ay[k] = fma(gx, x.y, ay[k]);
+                bx[k] = fma(-gy, x.y, bx[k]);
+                by[k] = fma(gy, x.x, by[k]);
+            }
+        }
+    } else {
+        for (int c = 0; c < J.n_c; ++c) {
+            const int ra = c * J.n + a;
+            const int pa0 = __ldg(J.crp + ra), pa1 = __ldg(J.crp + ra + 1);
+            for (int p = pa0; p < pa1; ++p) {
+                const TV u = __ldg(cv + p);
+                const T2* col = Y + (size_t)__ldg(J.cci + p);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int rb = c * J.n + b[k];
+                    for (int q = __ldg(J.crp + rb); q < __ldg(J.crp + rb + 1); ++q) {
+                        const TV w = __ldg(cv + q);
+                        const T gx = u.x * w.x + u.y * w.y, gy = u.y * w.x - u.x * w.y;
+                        const T2 x = __ldcg(col + n * (size_t)__ldg(J.cci + q));
+                        ax[k] = fma(gx, x.x, ax[k]);
+                        ay[k] = fma(gx, x.y, ay[k]);
+                        bx[k] = fma(-gy, x.y, bx[k]);
+                        by[k] = fma(gy, x.x, by[k]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        out[k].x = ax[k] + bx[k];
+        out[k].y = ay[k] + by[k];
+    }
 }
 
 // Sum of one float per block over the grid, in a fixed order, identical in
@@ -202,8 +353,10 @@ __device__ __forceinline__ float block_sum_f(float v, MgShared& sh) {
     return s;
 }
 
+// MIXED keeps two blocks (32 warps) per SM to hide the gather latency; FP64
+// needs the larger register budget of one block per SM.
 template <bool MIXED>
-__global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
+__global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
     using T = typename GPrec<MIXED>::T;
     using T2 = typename GPrec<MIXED>::T2;
     using TV = T2;
@@ -218,6 +371,7 @@ __global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
     const TV* av = MIXED ? (const TV*)J.av32 : (const TV*)J.av64;
     const TV* bv = MIXED ? (const TV*)J.bv32 : (const TV*)J.bv64;
     const TV* cv = MIXED ? (const TV*)J.cv32 : (const TV*)J.cv64;
+    const void* cmv = MIXED ? (const void*)J.cmv32 : (const void*)J.cmv64;
     T2* kbase = (T2*)J.k;
     T2* ysb[2] = {(T2*)J.ys, (T2*)J.ys + L};
     // State buffers (current / candidate, swapped on accept).  FP64: one
@@ -269,6 +423,13 @@ __global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
         }
     };
     int slot[7] = {0, 1, 2, 3, 4, 5, 6};
+    // right-hand-side phases: thread (ra, jg) owns row ra and the columns
+    // b = jg, jg + mcols, ... (n <= grid threads is required), processed four
+    // at a time
+    const int gtid = (int)g0;
+    const int mcols = (int)(G / (size_t)n);
+    const int ra = gtid % n, jg = gtid / n;
+    const bool ractive = jg < mcols;
     auto K = [&](int j) -> T2* { return kbase + (size_t)slot[j] * L; };
 
     // ---- initial state, k1 ----
@@ -285,8 +446,16 @@ __global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
         ysb[0][e] = g_from_d2<T2>(v);
     }
     grid.sync();
-    for (size_t e = g0; e < L; e += G)
-        K(0)[e] = rhs_entry<T2, TV>(J, ysb[0], (int)(e % n), (int)(e / n), av, bv, cv);
+    for (int b0 = jg; ractive && b0 < n; b0 += 4 * mcols) {
+        int bk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bk[q] = b0 + q * mcols < n ? b0 + q * mcols : b0;
+        T2 r[4];
+        rhs_row4<T2, TV>(J, ysb[0], ra, bk, r, av, bv, cv, cmv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (b0 + q * mcols < n) K(0)[(size_t)ra + (size_t)n * bk[q]] = r[q];
+    }
 
     // Tr(O_e rho) for rho = src, per-block FP64 partials -> epart[idx][block]
     auto expect_partials = [&](const S* src, int idx) {
@@ -364,14 +533,24 @@ __global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
         }
         grid.sync();
         float s2 = 0.f;
-        for (size_t e = g0; e < L; e += G) {
-            const double2 f1 = g_to_d2(rhs_entry<T2, TV>(J, ysb[1], (int)(e % n), (int)(e / n), av, bv, cv));
-            const double2 f0 = g_to_d2(K(0)[e]);
-            const double2 y = st_d2(yb, e);
-            const float sc = (float)J.atol + (float)J.rtol * sqrtf((float)(y.x * y.x + y.y * y.y));
-            const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
-            const float q = sqrtf(dx * dx + dy * dy) / sc;
-            s2 += q * q;
+        for (int b0 = jg; ractive && b0 < n; b0 += 4 * mcols) {
+            int bk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bk[q] = b0 + q * mcols < n ? b0 + q * mcols : b0;
+            T2 r[4];
+            rhs_row4<T2, TV>(J, ysb[1], ra, bk, r, av, bv, cv, cmv);
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                if (b0 + q4 * mcols >= n) continue;
+                const size_t e = (size_t)ra + (size_t)n * bk[q4];
+                const double2 f1 = g_to_d2(r[q4]);
+                const double2 f0 = g_to_d2(K(0)[e]);
+                const double2 y = st_d2(yb, e);
+                const float sc = (float)J.atol + (float)J.rtol * sqrtf((float)(y.x * y.x + y.y * y.y));
+                const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
+                const float q = sqrtf(dx * dx + dy * dy) / sc;
+                s2 += q * q;
+            }
         }
         float b2 = block_sum_f(s2, sh);
         __syncthreads();
@@ -484,8 +663,17 @@ __global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
             T he[7];
 #pragma unroll
             for (int j = 0; j < 7; ++j) he[j] = s == 6 ? coefT(21 + j) : (T)0;
-            for (size_t e = g0; e < L; e += G) {
-                const T2 ks = rhs_entry<T2, TV>(J, in, (int)(e % n), (int)(e / n), av, bv, cv);
+            for (int b0 = jg; ractive && b0 < n; b0 += 4 * mcols) {
+              int bk[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) bk[q] = b0 + q * mcols < n ? b0 + q * mcols : b0;
+              T2 r[4];
+              rhs_row4<T2, TV>(J, in, ra, bk, r, av, bv, cv, cmv);
+#pragma unroll
+              for (int q4 = 0; q4 < 4; ++q4) {
+                if (b0 + q4 * mcols >= n) continue;
+                const size_t e = (size_t)ra + (size_t)n * bk[q4];
+                const T2 ks = r[q4];
                 K(s)[e] = ks;
                 if (s < 6) {
                     // input of stage s+1: y + h sum_{j<=s} a_{s+1,j} k_j
@@ -526,6 +714,7 @@ __global__ void __launch_bounds__(MG_T) me_grid_kernel(MgJob J) {
                     const float fx = (float)ex, fy = (float)ey;
                     se += (fx * fx + fy * fy) / (sc * sc);
                 }
+              }
             }
             if (s < 6) grid.sync();
         }

@@ -220,16 +220,25 @@ static qtl_status upload_csr(const Csr& m, DevCsr& d) {
     std::vector<float2> v32(m.nnz());
     std::vector<int32_t> ci(m.nnz());
     std::vector<int4> seg(m.n);
+    std::vector<std::pair<int32_t, int64_t>> order;
     for (int r = 0; r < m.n; ++r) {
-        // group the row's entries: real-only, imaginary-only, complex
+        // group the row's entries: real-only, imaginary-only, complex; inside
+        // a group order them by col XOR row, so that in tensor-product
+        // operators the p-th entry of neighbouring rows is the same term and
+        // a warp's gathers stay in aligned blocks
         int32_t q = m.rp[r];
         int b[3];
         for (int grp = 0; grp < 3; ++grp) {
             b[grp] = q;
+            order.clear();
             for (int64_t p = m.rp[r]; p < m.rp[r + 1]; ++p) {
                 const bool re0 = m.re[p] == 0.0, im0 = m.im[p] == 0.0;
                 const int gp = im0 ? 0 : (re0 ? 1 : 2);
-                if (gp != grp) continue;
+                if (gp == grp) order.emplace_back(m.ci[p] ^ r, p);
+            }
+            std::sort(order.begin(), order.end());
+            for (const auto& kp : order) {
+                const int64_t p = kp.second;
                 ci[q] = m.ci[p];
                 v64[q] = make_double2(m.re[p], m.im[p]);
                 v32[q] = make_float2((float)m.re[p], (float)m.im[p]);
@@ -349,6 +358,9 @@ qtl_status mesolve_grid(System& s, const qtl_c128* state0_dev, int32_t is_ket, c
     J.cci = s.dC.ci;
     J.cv64 = s.dC.v64;
     J.cv32 = s.dC.v32;
+    J.cmap = s.cmap;
+    J.cmv64 = s.cval64;
+    J.cmv32 = s.cval32;
     J.n_e = s.n_e;
     J.orp = s.dO.rp;
     J.oci = s.dO.ci;
@@ -438,6 +450,9 @@ void qtl_system_free(qtl_system* sys) {
     System& s = sys->s;
     free_csr(s.dA);
     free_csr(s.dBt);
+    cudaFree(s.cmap);
+    cudaFree(s.cval64);
+    cudaFree(s.cval32);
     free_csr(s.dC);
     free_csr(s.dO);
     free_csr(s.dL);
@@ -476,6 +491,30 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c, 
     Csr Cs, Os;
     stack(s.C, s.n, Cs);
     stack(s.O, s.n, Os);
+    // Collapse operators with at most one entry per row (sigma-, a, projectors,
+    // ...): dense per-row column maps for the grid kernel's C rho C^dag.
+    bool monomial = s.n_c > 0;
+    for (const Csr& c : s.C)
+        for (int i = 0; i < s.n && monomial; ++i)
+            if (c.rp[i + 1] - c.rp[i] > 1) monomial = false;
+    if (monomial) {
+        std::vector<int32_t> cmap((size_t)s.n_c * s.n, -1);
+        std::vector<double2> cval64((size_t)s.n_c * s.n, make_double2(0.0, 0.0));
+        std::vector<float2> cval32((size_t)s.n_c * s.n, make_float2(0.f, 0.f));
+        for (int c = 0; c < s.n_c; ++c)
+            for (int i = 0; i < s.n; ++i)
+                for (int64_t p = s.C[c].rp[i]; p < s.C[c].rp[i + 1]; ++p) {
+                    cmap[(size_t)c * s.n + i] = s.C[c].ci[p];
+                    cval64[(size_t)c * s.n + i] = make_double2(s.C[c].re[p], s.C[c].im[p]);
+                    cval32[(size_t)c * s.n + i] = make_float2((float)s.C[c].re[p], (float)s.C[c].im[p]);
+                }
+        if ((st = upload(&s.cmap, cmap.data(), cmap.size())) != QTL_OK ||
+            (st = upload(&s.cval64, cval64.data(), cval64.size())) != QTL_OK ||
+            (st = upload(&s.cval32, cval32.data(), cval32.size())) != QTL_OK) {
+            qtl_system_free(sys);
+            return st;
+        }
+    }
     if ((st = upload_csr(s.A, s.dA)) != QTL_OK || (st = upload_csr(s.Bt, s.dBt)) != QTL_OK ||
         (st = upload_csr(Cs, s.dC)) != QTL_OK ||
         (st = upload_csr(Os, s.dO)) != QTL_OK) {

@@ -135,14 +135,19 @@ def test_edge_cases():
     g3.free()
 
 
-def test_too_big_is_refused():
+def test_too_big_for_a_cluster():
+    """n*n = 262144 is beyond one cluster: forcing the cluster kernel is refused
+    with a status, the automatic choice runs it on the grid kernel."""
     qtl = require_gpu()
-    s = W.ising_chain(8, h=1.0)   # L = 65536 fits; 9 spins do not
-    g = qtl.System(W.ising_chain(9, h=1.0).H, [], [])
+    s = W.ising_chain(9, h=1.0)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
     with pytest.raises(qtl.QtlError) as e:
-        g.mesolve(np.eye(512)[0].astype(complex), np.array([0.0, 0.1]))
+        g.mesolve(s.psi0, np.array([0.0, 0.1]), engine="cluster")
     assert e.value.status == qtl.QTL_ETOOBIG
+    out = g.mesolve(s.psi0, np.array([0.0, 0.05, 0.1]), precision="mixed", rtol=1e-7, atol=1e-9)
     g.free()
+    assert np.all(np.isfinite(out["expect"]))
+    assert abs(out["expect"][2, 0].real - 9.0) < 1e-12   # all spins up at t = 0
 
 
 def test_async_device_path_matches_host_path():
