@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--impl", default="qtl", choices=["qtl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="jc_40x2", choices=["jc_40x2", "kerr_sweep_1024"])
+    ap.add_argument("--workload", default="jc_40x2", choices=["jc_40x2", "kerr_sweep_1024", "serving"])
+    ap.add_argument("--rates", default="10,30,100,300")
+    ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -420,8 +422,61 @@ def run_sweep(args):
         h.free()
 
 
+def run_serving(args):
+    """Serving: Poisson arrivals of mixed requests at each rate -- 60%
+    mesolve on coupled-cavity pairs (N1, N2 ~ U{4..32}, J ~ U[0,1],
+    kappa_i ~ U[0.01,0.3], rho0 = |1,0>, t in [0,20], 101 points) and 40%
+    mcsolve on Ising chains (8-10 spins, 100-2000 trajectories, t in [0,10],
+    101 points), mixed precision, rtol 1e-7, atol 1e-9 -- submitted to one
+    qtl server (HBM budget 90% of free memory, 8 requests in flight).
+    Latency = completion - arrival."""
+    import threading as th
+    import torch
+    from paper_2504_21440_gb300 import qtl
+    torch.cuda.set_device(0)
+    qtl.load()
+    opts = qtl.make_opts(precision="mixed", rtol=1e-7, atol=1e-9)
+    lines = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        reqs = W.serving_mix(n_requests=args.requests, seed=5, rate=rate, ising_spins=(8, 10))
+        systems = [qtl.System(r["system"].H, r["system"].c_ops, r["system"].e_ops) for r in reqs]
+        srv = qtl.Server(max_inflight=8)
+        # warm-up: one request of each kind
+        for r, g in list(zip(reqs, systems))[:4]:
+            srv.wait(srv.submit(r["kind"], g, r["system"].psi0, r["system"].tlist, opts,
+                                ntraj=r.get("ntraj", 0), seed=r.get("seed", 0)))
+        tickets = [None] * len(reqs)
+        t0 = time.perf_counter()
+        for i, (r, g) in enumerate(zip(reqs, systems)):
+            dt = t0 + r["arrival"] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = (time.perf_counter(), srv.submit(r["kind"], g, r["system"].psi0, r["system"].tlist,
+                                                          opts, ntraj=r.get("ntraj", 0), seed=r.get("seed", 0)))
+        res = [srv.wait(t) for _, t in tickets]
+        t1 = time.perf_counter()
+        srv.free()
+        for g in systems:
+            g.free()
+        mono0 = time.monotonic() - time.perf_counter()   # perf_counter -> steady clock offset
+        lat = sorted(1e3 * (r["t_end"] - (t0 + rq["arrival"] + mono0)) for r, rq in zip(res, reqs))
+        bad = sum(1 for r in res if r["status"] != 0)
+        lines.append({"rate_req_per_s": rate, "requests": len(reqs), "failed": bad,
+                      "solves_per_s": len(reqs) / (t1 - t0),
+                      "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                     "max": lat[-1]},
+                      "mix": {"mesolve": sum(r["kind"] == "mesolve" for r in reqs),
+                              "mcsolve": sum(r["kind"] == "mcsolve" for r in reqs)}})
+    print(json.dumps({"metric": "p50/p99 solve latency and solves/s under Poisson arrivals",
+                      "workload": "serving mix: coupled-cavity mesolve (n 16-1024) + Ising mcsolve (8-10 spins)",
+                      "dtype": "f32 RHS / f64 state", "data": "synthetic", "n_gpus": 1, "rates": lines}))
+
+
 def main():
     args = parse()
+    if args.workload == "serving" and args.impl != "reference":
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "kerr_sweep_1024":

@@ -224,6 +224,60 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
                              const qtl_opts* opts, qtl_c128* expect_dev,
                              qtl_c128* traj_expect_dev, qtl_device_info* info_dev);
 
+/* ------------------------------------------------------------- serving ---
+ * A request server (no counterpart in the paper; it serves the mesolve and
+ * mcsolve calls above).  Requests are queued on submit and admitted in
+ * arrival order while their estimated device memory fits the HBM budget;
+ * each admitted request runs on its own CUDA stream, so requests that arrive
+ * while others are on the GPU are admitted as memory frees up and their
+ * kernels overlap.  Results are those of the corresponding qtl_mesolve /
+ * qtl_mcsolve call, bit for bit (each solve's arithmetic depends only on its
+ * own inputs).  The caller's host buffers (state0, tlist, expect_out) must
+ * stay valid until the request is done; the system must outlive it. */
+typedef struct qtl_server qtl_server;
+
+enum { QTL_REQ_MESOLVE = 0, QTL_REQ_MCSOLVE = 1 };
+
+typedef struct {
+    int32_t kind;            /* QTL_REQ_MESOLVE | QTL_REQ_MCSOLVE */
+    qtl_system* sys;
+    const qtl_c128* state0;  /* host: ket (n) or, for mesolve with is_ket = 0, vec(rho0) */
+    int32_t is_ket;
+    const double* tlist;     /* host, nt entries */
+    int32_t nt;
+    int32_t ntraj;           /* mcsolve */
+    uint64_t seed;           /* mcsolve */
+    qtl_opts opts;           /* cuda_stream is ignored: the server owns its streams */
+} qtl_request;
+
+typedef struct {
+    int32_t status;          /* qtl_status of the solve (QTL_EBUSY while running) */
+    int32_t pad;
+    qtl_stats stats;
+    double t_submit;         /* seconds on a monotonic clock */
+    double t_start;          /* admitted and enqueued */
+    double t_end;            /* results in the caller's buffer */
+} qtl_result;
+
+/* hbm_budget_bytes: device memory the server may hold for requests at once
+ * (0 = 90% of the device's free memory); max_inflight: streams (1..64). */
+qtl_status qtl_server_create(size_t hbm_budget_bytes, int32_t max_inflight, qtl_server** out);
+/* Queues a request; expect_out (host, n_e*nt) receives the expectation values.
+ * QTL_ENOMEM if the request alone exceeds the budget, QTL_EINVAL on bad input. */
+qtl_status qtl_server_submit(qtl_server* srv, const qtl_request* req, qtl_c128* expect_out,
+                             uint64_t* ticket);
+/* QTL_EBUSY while the request is queued or running, else QTL_OK with *out filled. */
+qtl_status qtl_server_poll(qtl_server* srv, uint64_t ticket, qtl_result* out);
+/* Blocks until the request is done. */
+qtl_status qtl_server_wait(qtl_server* srv, uint64_t ticket, qtl_result* out);
+/* Removes a request that has not been admitted yet (its result becomes
+ * QTL_ECANCEL); QTL_EBUSY if it is already running. */
+qtl_status qtl_server_cancel(qtl_server* srv, uint64_t ticket);
+/* Device bytes currently held for admitted requests, and requests waiting. */
+qtl_status qtl_server_usage(qtl_server* srv, size_t* bytes_in_use, int32_t* queued, int32_t* running);
+/* Waits for running requests, cancels queued ones, releases everything. */
+void qtl_server_free(qtl_server* srv);
+
 /* No counterpart in the paper: an mcsolve entry point for callers that cannot
  * allocate device memory while they solve -- code running during CUDA stream
  * capture (cudaMalloc is not allowed there), processes whose device memory is

@@ -1,0 +1,339 @@
+// Request server (qtl_server_*): a queue of mesolve / mcsolve requests
+// admitted in arrival order while their estimated device memory fits an HBM
+// budget, each admitted request running on its own CUDA stream so that work
+// from requests that arrived at different times overlaps on the GPU.
+//
+// One dispatcher thread owns the CUDA work: it admits requests (device
+// buffers from the stream-ordered pool, host->device copies, the _async
+// solve, device->host copies into a pinned per-slot staging buffer, the
+// stream-ordered free, a completion event), and retires them when their
+// event has completed (copy from staging to the caller's buffer, release of
+// the budget and the slot).  Submit / poll / wait / cancel only touch the
+// queue under a mutex.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace qtl {
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct SrvReq {
+    uint64_t ticket = 0;
+    qtl_request r{};
+    qtl_c128* expect_out = nullptr;
+    size_t bytes = 0;
+    size_t ex_bytes = 0;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int slot = -1;
+    qtl_result res{};
+};
+
+struct SrvSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    void* pinned = nullptr;   // staging: device info, then the expectation values
+    size_t pinned_bytes = 0;
+    SrvReq* req = nullptr;
+};
+
+}  // namespace qtl
+
+struct qtl_server {
+    int device = 0;
+    size_t budget = 0, in_use = 0;
+    std::vector<qtl::SrvSlot> slots;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, qtl::SrvReq*> reqs;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    int running = 0;
+};
+
+namespace qtl {
+
+// Device bytes a request will hold while it runs (inputs, outputs and the
+// solver's scratch), used for admission.
+static size_t request_bytes(const qtl_request& r) {
+    const System& s = r.sys->s;
+    const size_t n = (size_t)s.n, L = n * n, nt = (size_t)r.nt, ne = (size_t)(s.n_e > 0 ? s.n_e : 1);
+    const size_t t2 = r.opts.precision == QTL_MIXED ? 8 : 16;
+    size_t b = (r.is_ket || r.kind == QTL_REQ_MCSOLVE ? n : L) * 16 + nt * 8 + ne * nt * 16 + 4096;
+    if (r.kind == QTL_REQ_MCSOLVE) {
+        b += ne * nt * (size_t)r.ntraj * 16;
+    } else if (L <= (size_t)me_cluster_capacity() && r.opts.engine != QTL_ENGINE_GRID) {
+        b += nt * 16 * 2 * ne * 8 + L * 40;  // expectation partials; Liouvillian if built here
+    } else {
+        b += 2 * L * 16 + 9 * L * t2 + nt * 2 * 304 * ne * 8;
+    }
+    return b;
+}
+
+static void srv_admit(qtl_server* S, SrvReq* q, int slot) {
+    SrvSlot& sl = S->slots[slot];
+    const System& s = q->r.sys->s;
+    cudaStream_t st = sl.stream;
+    const size_t n = (size_t)s.n, nt = (size_t)q->r.nt;
+    const size_t n0 = (q->r.kind == QTL_REQ_MCSOLVE || q->r.is_ket) ? n : n * n;
+    q->ex_bytes = (size_t)s.n_e * nt * 16;
+    const size_t need_pinned = 64 + q->ex_bytes;
+    q->slot = slot;
+    q->state = 1;
+    q->res.t_start = now_s();
+    sl.req = q;
+    qtl_status stt = QTL_OK;
+    if (sl.pinned_bytes < need_pinned) {
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+        sl.pinned = nullptr;
+        sl.pinned_bytes = 0;
+        if (cudaMallocHost(&sl.pinned, need_pinned) == cudaSuccess) sl.pinned_bytes = need_pinned;
+        else stt = QTL_ENOMEM;
+    }
+    char* dbuf = nullptr;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t o_st = 0, o_tl = up(n0 * 16), o_ex = o_tl + up(nt * 8), o_inf = o_ex + up(q->ex_bytes + 16);
+    const size_t total = o_inf + 256;
+    if (stt == QTL_OK && cudaMallocAsync((void**)&dbuf, total, st) != cudaSuccess) stt = QTL_ENOMEM;
+    if (stt == QTL_OK) {
+        cudaMemcpyAsync(dbuf + o_st, q->r.state0, n0 * 16, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(dbuf + o_tl, q->r.tlist, nt * 8, cudaMemcpyHostToDevice, st);
+        qtl_opts o = q->r.opts;
+        o.cuda_stream = st;
+        qtl_device_info* dinfo = (qtl_device_info*)(dbuf + o_inf);
+        if (q->r.kind == QTL_REQ_MESOLVE)
+            stt = qtl_mesolve_async(q->r.sys, (const qtl_c128*)(dbuf + o_st), q->r.is_ket,
+                                    (const double*)(dbuf + o_tl), q->r.nt, &o,
+                                    (qtl_c128*)(dbuf + o_ex), nullptr, dinfo);
+        else
+            stt = qtl_mcsolve_async(q->r.sys, (const qtl_c128*)(dbuf + o_st),
+                                    (const double*)(dbuf + o_tl), q->r.nt, q->r.ntraj, q->r.seed, 0, &o,
+                                    (qtl_c128*)(dbuf + o_ex), nullptr, dinfo);
+        if (stt == QTL_OK) {
+            cudaMemcpyAsync(sl.pinned, dinfo, sizeof(qtl_device_info), cudaMemcpyDeviceToHost, st);
+            if (q->ex_bytes)
+                cudaMemcpyAsync((char*)sl.pinned + 64, dbuf + o_ex, q->ex_bytes, cudaMemcpyDeviceToHost, st);
+        }
+        cudaFreeAsync(dbuf, st);
+    }
+    if (stt != QTL_OK) {
+        // nothing to wait for beyond what is already enqueued on the stream
+        qtl_device_info fail{};
+        fail.status = stt;
+        if (sl.pinned) std::memcpy(sl.pinned, &fail, sizeof(fail));
+        q->res.status = stt;
+    }
+    cudaEventRecord(sl.done, st);
+}
+
+static void srv_retire(qtl_server* S, int slot) {
+    SrvSlot& sl = S->slots[slot];
+    SrvReq* q = sl.req;
+    qtl_device_info info{};
+    if (sl.pinned) std::memcpy(&info, sl.pinned, sizeof(info));
+    if (q->res.status == QTL_OK || q->res.status == QTL_EBUSY) q->res.status = info.status;
+    q->res.stats.steps_acc = info.steps_acc;
+    q->res.stats.steps_rej = info.steps_rej;
+    q->res.stats.rhs_evals = info.rhs_evals;
+    q->res.stats.jumps = info.jumps;
+    if (q->ex_bytes && q->res.status == QTL_OK && q->expect_out)
+        std::memcpy(q->expect_out, (char*)sl.pinned + 64, q->ex_bytes);
+    q->res.t_end = now_s();
+    q->state = 2;
+    sl.req = nullptr;
+    S->in_use -= q->bytes;
+    S->running -= 1;
+}
+
+static void srv_loop(qtl_server* S) {
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        bool progressed = false;
+        for (size_t i = 0; i < S->slots.size(); ++i) {
+            if (S->slots[i].req && cudaEventQuery(S->slots[i].done) == cudaSuccess) {
+                srv_retire(S, (int)i);
+                progressed = true;
+            }
+        }
+        if (progressed) S->cv_done.notify_all();
+        // admit in arrival order while memory and a slot are free
+        while (!S->queue.empty()) {
+            SrvReq* q = S->reqs[S->queue.front()];
+            if (S->in_use + q->bytes > S->budget) break;
+            int slot = -1;
+            for (size_t i = 0; i < S->slots.size(); ++i)
+                if (!S->slots[i].req) {
+                    slot = (int)i;
+                    break;
+                }
+            if (slot < 0) break;
+            S->queue.pop_front();
+            S->in_use += q->bytes;
+            S->running += 1;
+            srv_admit(S, q, slot);
+        }
+        if (S->stop && S->running == 0) break;
+        if (S->running > 0)
+            S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        else
+            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
+    }
+}
+
+}  // namespace qtl
+
+using namespace qtl;
+
+extern "C" {
+
+qtl_status qtl_server_create(size_t hbm_budget_bytes, int32_t max_inflight, qtl_server** out) {
+    if (!out || max_inflight < 1 || max_inflight > 64) return QTL_EINVAL;
+    *out = nullptr;
+    qtl_server* S = new qtl_server();
+    cudaGetDevice(&S->device);
+    if (hbm_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            delete S;
+            return QTL_ECUDA;
+        }
+        hbm_budget_bytes = fr / 10 * 9;
+    }
+    S->budget = hbm_budget_bytes;
+    S->slots.resize(max_inflight);
+    for (auto& sl : S->slots) {
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto& x : S->slots) {
+                if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.done) cudaEventDestroy(x.done);
+            }
+            delete S;
+            return QTL_ECUDA;
+        }
+    }
+    S->worker = std::thread(srv_loop, S);
+    *out = S;
+    return QTL_OK;
+}
+
+qtl_status qtl_server_submit(qtl_server* S, const qtl_request* req, qtl_c128* expect_out,
+                             uint64_t* ticket) {
+    if (!S || !req || !ticket || !req->sys || !req->state0 || !req->tlist || req->nt < 1) return QTL_EINVAL;
+    if (req->kind != QTL_REQ_MESOLVE && req->kind != QTL_REQ_MCSOLVE) return QTL_EINVAL;
+    if (req->kind == QTL_REQ_MCSOLVE && req->ntraj < 1) return QTL_EINVAL;
+    if (req->sys->s.n_e > 0 && !expect_out) return QTL_EINVAL;
+    qtl_status st = validate_opts(&req->opts);
+    if (st != QTL_OK) return st;
+    for (int i = 1; i < req->nt; ++i)
+        if (!(req->tlist[i] >= req->tlist[i - 1])) return QTL_EINVAL;
+    SrvReq* q = new SrvReq();
+    q->r = *req;
+    q->expect_out = expect_out;
+    q->bytes = request_bytes(*req);
+    q->res.status = QTL_EBUSY;
+    q->res.t_submit = now_s();
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (q->bytes > S->budget) {
+        delete q;
+        return QTL_ENOMEM;
+    }
+    q->ticket = S->next_ticket++;
+    S->reqs[q->ticket] = q;
+    S->queue.push_back(q->ticket);
+    *ticket = q->ticket;
+    S->cv_work.notify_one();
+    return QTL_OK;
+}
+
+static qtl_status take_result(qtl_server* S, uint64_t ticket, qtl_result* out) {
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return QTL_EINVAL;
+    SrvReq* q = it->second;
+    if (q->state != 2) return QTL_EBUSY;
+    if (out) *out = q->res;
+    delete q;
+    S->reqs.erase(it);
+    return QTL_OK;
+}
+
+qtl_status qtl_server_poll(qtl_server* S, uint64_t ticket, qtl_result* out) {
+    if (!S) return QTL_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    return take_result(S, ticket, out);
+}
+
+qtl_status qtl_server_wait(qtl_server* S, uint64_t ticket, qtl_result* out) {
+    if (!S) return QTL_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        qtl_status st = take_result(S, ticket, out);
+        if (st != QTL_EBUSY) return st;
+        S->cv_done.wait(lk);
+    }
+}
+
+qtl_status qtl_server_cancel(qtl_server* S, uint64_t ticket) {
+    if (!S) return QTL_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return QTL_EINVAL;
+    SrvReq* q = it->second;
+    if (q->state != 0) return QTL_EBUSY;
+    for (auto qi = S->queue.begin(); qi != S->queue.end(); ++qi)
+        if (*qi == ticket) {
+            S->queue.erase(qi);
+            break;
+        }
+    q->state = 2;
+    q->res.status = QTL_ECANCEL;
+    q->res.t_end = now_s();
+    S->cv_done.notify_all();
+    return QTL_OK;
+}
+
+qtl_status qtl_server_usage(qtl_server* S, size_t* bytes_in_use, int32_t* queued, int32_t* running) {
+    if (!S) return QTL_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (bytes_in_use) *bytes_in_use = S->in_use;
+    if (queued) *queued = (int32_t)S->queue.size();
+    if (running) *running = S->running;
+    return QTL_OK;
+}
+
+void qtl_server_free(qtl_server* S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (uint64_t t : S->queue) {
+            SrvReq* q = S->reqs[t];
+            q->state = 2;
+            q->res.status = QTL_ECANCEL;
+        }
+        S->queue.clear();
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    for (auto& kv : S->reqs) delete kv.second;
+    for (auto& sl : S->slots) {
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+    }
+    delete S;
+}
+
+}  // extern "C"

@@ -48,6 +48,17 @@ class Stats(C.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("sys", C.c_void_p), ("state0", C.c_void_p), ("is_ket", C.c_int32),
+                ("tlist", C.c_void_p), ("nt", C.c_int32), ("ntraj", C.c_int32), ("seed", C.c_uint64),
+                ("opts", Opts)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("stats", Stats), ("t_submit", C.c_double),
+                ("t_start", C.c_double), ("t_end", C.c_double)]
+
+
 class DeviceInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("steps_acc", C.c_int64),
                 ("steps_rej", C.c_int64), ("rhs_evals", C.c_int64), ("jumps", C.c_int64)]
@@ -99,6 +110,20 @@ def load():
                                         C.c_int32, P, P, P, P, P, C.c_int32, C.c_int32,
                                         C.c_uint64, C.c_int64, C.POINTER(Opts), P, P]
     lib.qtl_mcsolve_noalloc.restype = C.c_int
+    lib.qtl_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(P)]
+    lib.qtl_server_create.restype = C.c_int
+    lib.qtl_server_submit.argtypes = [P, C.POINTER(Request), P, C.POINTER(C.c_uint64)]
+    lib.qtl_server_submit.restype = C.c_int
+    lib.qtl_server_poll.argtypes = [P, C.c_uint64, C.POINTER(Result)]
+    lib.qtl_server_poll.restype = C.c_int
+    lib.qtl_server_wait.argtypes = [P, C.c_uint64, C.POINTER(Result)]
+    lib.qtl_server_wait.restype = C.c_int
+    lib.qtl_server_cancel.argtypes = [P, C.c_uint64]
+    lib.qtl_server_cancel.restype = C.c_int
+    lib.qtl_server_usage.argtypes = [P, C.POINTER(C.c_size_t), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.qtl_server_usage.restype = C.c_int
+    lib.qtl_server_free.argtypes = [P]
+    lib.qtl_server_free.restype = None
     lib.qtl_strerror.argtypes = [C.c_int]
     lib.qtl_strerror.restype = C.c_char_p
     lib.qtl_last_cuda_error.argtypes = []
@@ -296,6 +321,64 @@ def mesolve_batch_async(handles, states_dev, is_ket, tlist_dev, opts, expects_de
     _check(load().qtl_mesolve_batch_async(harr, nb, sarr, karr, _ptr(tlist_dev), int(tlist_dev.numel()),
                                           C.byref(opts), earr, _ptr(info_dev)), "qtl_mesolve_batch_async")
     return (harr, sarr, karr, earr)
+
+
+class Server:
+    """qtl_server_*: a request queue admitted by HBM budget, requests running
+    concurrently on the server's streams.  submit() keeps the request's host
+    buffers alive until its result has been taken."""
+
+    def __init__(self, hbm_budget_bytes=0, max_inflight=8):
+        self.handle = C.c_void_p()
+        _check(load().qtl_server_create(int(hbm_budget_bytes), int(max_inflight), C.byref(self.handle)),
+               "qtl_server_create")
+        self._keep = {}
+
+    def submit(self, kind, system, state0, tlist, opts, ntraj=0, seed=0):
+        st = np.ascontiguousarray(state0, dtype=np.complex128)
+        is_ket = 1 if st.ndim == 1 and len(st) == system.n else 0
+        if st.ndim == 2:
+            st = np.ascontiguousarray(st.reshape(-1, order="F"))
+        tl = np.ascontiguousarray(tlist, dtype=np.float64)
+        ex = np.zeros((max(system.n_e, 1), len(tl)), dtype=np.complex128)
+        req = Request(0 if kind == "mesolve" else 1, system.handle, st.ctypes.data, is_ket, tl.ctypes.data,
+                      len(tl), int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)), opts)
+        t = C.c_uint64()
+        _check(load().qtl_server_submit(self.handle, C.byref(req), ex.ctypes.data, C.byref(t)),
+               "qtl_server_submit")
+        self._keep[t.value] = (st, tl, ex, system.n_e)
+        return t.value
+
+    def _take(self, ticket, res):
+        st, tl, ex, ne = self._keep.pop(ticket)
+        return dict(status=int(res.status), expect=ex[:ne], stats=res.stats.as_dict(),
+                    t_submit=res.t_submit, t_start=res.t_start, t_end=res.t_end)
+
+    def poll(self, ticket):
+        res = Result()
+        s = load().qtl_server_poll(self.handle, C.c_uint64(ticket), C.byref(res))
+        if s == QTL_EBUSY:
+            return None
+        _check(s, "qtl_server_poll")
+        return self._take(ticket, res)
+
+    def wait(self, ticket):
+        res = Result()
+        _check(load().qtl_server_wait(self.handle, C.c_uint64(ticket), C.byref(res)), "qtl_server_wait")
+        return self._take(ticket, res)
+
+    def cancel(self, ticket):
+        return load().qtl_server_cancel(self.handle, C.c_uint64(ticket))
+
+    def usage(self):
+        b, q, r = C.c_size_t(), C.c_int32(), C.c_int32()
+        _check(load().qtl_server_usage(self.handle, C.byref(b), C.byref(q), C.byref(r)), "qtl_server_usage")
+        return b.value, q.value, r.value
+
+    def free(self):
+        if self.handle:
+            load().qtl_server_free(self.handle)
+            self.handle = None
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
