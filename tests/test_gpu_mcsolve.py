@@ -106,3 +106,20 @@ def test_mcsolve_edge_cases():
     assert out["stats"]["jumps"] == 0
     assert maxabs(out["expect"][0].real, np.cos(2 * np.linspace(0, 3, 7))) < 1e-8
     g2.free()
+
+
+def test_sharded_ranges_reproduce_the_full_ensemble():
+    """Two trajectory shares (as two ranks would run them) combine to the
+    single-call ensemble mean."""
+    from paper_2504_21440_gb300.shard import trajectory_shard
+    qtl = require_gpu()
+    s = W.jaynes_cummings(N=5, nt=21, t_end=60.0, kappa=0.1)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    full = g.mcsolve(s.psi0, s.tlist, 101, 3)
+    acc = 0
+    for r in range(2):
+        first, count = trajectory_shard(101, r, 2)
+        part = g.mcsolve(s.psi0, s.tlist, count, 3, traj_offset=first)
+        acc = acc + part["expect"] * count
+    g.free()
+    assert maxabs(acc / 101, full["expect"]) <= 1e-13
