@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="qtl", choices=["qtl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="jc_40x2", choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10"])
+    ap.add_argument("--workload", default="jc_40x2",
+                    choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc"])
     ap.add_argument("--rates", default="10,30,100,300")
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -489,11 +490,88 @@ def run_ising10(args):
     g.free()
 
 
+def run_ising14_mc(args):
+    """mcsolve on the dissipative transverse-field Ising chain of 14 spins
+    (n = 16,384; H_eff with 245,760 entries), h from seed 3, gamma = 0.1, all
+    spins excited, tlist range(0, 10, 100), 2000 trajectories, mixed
+    precision, rtol 1e-7, atol 1e-9: one mcsolve (the wide trajectory kernel,
+    one 1024-thread CTA per trajectory) per step.  Value: trajectories per
+    second.  Roofline: the integrator's state bytes per attempted step and row
+    -- per stage s < 6 the FP32 state copy (8 B) and s derivatives (8 B each)
+    read and the new derivative written (8 B); at the sixth stage the FP64
+    state read and y_new written (2 x 16 B), its FP32 copy (8 B), 6
+    derivatives read (48 B), the error partial and scale written and read
+    back (2 x 12 B) and the last derivative written (8 B) -- 320 B in all,
+    against the measured copy bandwidth (H_eff itself is shared by all
+    trajectories and stays in L2)."""
+    import torch
+    from paper_2504_21440_gb300 import qtl
+    torch.cuda.set_device(0)
+    qtl.load()
+    dev = torch.device("cuda", 0)
+    s = W.ising_chain(14)
+    ntraj = 2000
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    psi = torch.from_numpy(s.psi0).to(dev)
+    tl = torch.from_numpy(s.tlist).to(dev)
+    ex = torch.zeros((3, len(s.tlist)), dtype=torch.complex128, device=dev)
+    tex = torch.zeros((3, len(s.tlist), ntraj), dtype=torch.complex128, device=dev)
+    info = torch.zeros(5, dtype=torch.int64, device=dev)
+    main = torch.cuda.current_stream(dev)
+    o = qtl.make_opts(precision="mixed", rtol=1e-7, atol=1e-9, stream=main.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        qtl.mcsolve_async(g.handle, psi, tl, 152, SEED, o, ex, tex, info)
+        torch.cuda.synchronize(dev)
+    ms, atts = [], []
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = qtl.launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        qtl.mcsolve_async(g.handle, psi, tl, ntraj, SEED, o, ex, tex, info)
+        e1.record(main)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+        inf = info.cpu().numpy()
+        atts.append(int(inf[1] + inf[2]))
+    clk = clocks.stop()
+    launches = qtl.launch_count() - l0
+    mean_ms = statistics.mean(ms)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = 320.0 * s.n * statistics.mean(atts) / (mean_ms / 1e3) / 1e9
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", "mc_wide.cu"),
+                                   os.path.join(ROOT, "profiles", "mc_wide_kernel_ising14_mixed.md"))
+    print(json.dumps({
+        "metric": "mcsolve traj/s (14-spin Ising, n = 16384, 2000 trajectories)",
+        "value": ntraj / (mean_ms / 1e3), "unit": "traj/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 RHS / f64 state", "data": "synthetic",
+        "config": {"workload": "ising14 mcsolve: J=1, h=U[0.5,1.5] seed 3, gamma=0.1, t in [0,10], "
+                               "100 saveat, 2000 trajectories, mixed, rtol 1e-7 atol 1e-9",
+                   "l2": "flushed (512 MB write) between timed steps; per-CTA state 1.9 MB x 152 > L2"},
+        "attempted_steps_per_traj": statistics.mean(atts) / ntraj, "jumps": int(inf[4]),
+        "status": int(inf[0]) & 0xffffffff, "Sz_t10": float(ex[2, -1].real),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "mc_wide_kernel",
+                     "note": "algorithmic 320 B/row/attempt of state; latency-bound (see profiles)"},
+        "gpu_launches": launches, "clocks": clk}))
+    g.free()
+
+
 def run_serving(args):
     """Serving: Poisson arrivals of mixed requests at each rate -- 60%
     mesolve on coupled-cavity pairs (N1, N2 ~ U{4..32}, J ~ U[0,1],
     kappa_i ~ U[0.01,0.3], rho0 = |1,0>, t in [0,20], 101 points) and 40%
-    mcsolve on Ising chains (8-10 spins, 100-2000 trajectories, t in [0,10],
+    mcsolve on Ising chains (8-14 spins, 100-2000 trajectories, t in [0,10],
     101 points), mixed precision, rtol 1e-7, atol 1e-9 -- submitted to one
     qtl server (HBM budget 90% of free memory, 8 requests in flight).
     Latency = completion - arrival."""
@@ -505,7 +583,7 @@ def run_serving(args):
     opts = qtl.make_opts(precision="mixed", rtol=1e-7, atol=1e-9)
     lines = []
     for rate in [float(x) for x in args.rates.split(",")]:
-        reqs = W.serving_mix(n_requests=args.requests, seed=5, rate=rate, ising_spins=(8, 10))
+        reqs = W.serving_mix(n_requests=args.requests, seed=5, rate=rate, ising_spins=(8, 14))
         systems = [qtl.System(r["system"].H, r["system"].c_ops, r["system"].e_ops) for r in reqs]
         srv = qtl.Server(max_inflight=8)
         # warm-up: one request of each kind
@@ -535,7 +613,7 @@ def run_serving(args):
                       "mix": {"mesolve": sum(r["kind"] == "mesolve" for r in reqs),
                               "mcsolve": sum(r["kind"] == "mcsolve" for r in reqs)}})
     print(json.dumps({"metric": "p50/p99 solve latency and solves/s under Poisson arrivals",
-                      "workload": "serving mix: coupled-cavity mesolve (n 16-1024) + Ising mcsolve (8-10 spins)",
+                      "workload": "serving mix: coupled-cavity mesolve (n 16-1024) + Ising mcsolve (8-14 spins)",
                       "dtype": "f32 RHS / f64 state", "data": "synthetic", "n_gpus": 1, "rates": lines}))
 
 
@@ -546,6 +624,9 @@ def main():
         return
     if args.workload == "ising10" and args.impl != "reference":
         run_ising10(args)
+        return
+    if args.workload == "ising14_mc" and args.impl != "reference":
+        run_ising14_mc(args)
         return
     if args.impl == "reference":
         run_reference(args)

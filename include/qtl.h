@@ -89,7 +89,10 @@ enum { QTL_FP64 = 0, QTL_MIXED = 1 };
  *                 kernel), QTL_ENGINE_CLUSTER (CSR Liouvillian in one thread-
  *                 block cluster; QTL_ETOOBIG if it does not fit) or
  *                 QTL_ENGINE_GRID (product form A rho + rho B + sum C rho C^dag
- *                 over a cooperative grid; no Liouvillian is formed) */
+ *                 over a cooperative grid; no Liouvillian is formed).
+ *                 mcsolve: AUTO (trajectory state in registers up to n = 1024,
+ *                 else in global memory), CLUSTER (registers; QTL_ETOOBIG
+ *                 above n = 1024) or GRID (global memory at any n) */
 enum { QTL_ENGINE_AUTO = 0, QTL_ENGINE_CLUSTER = 1, QTL_ENGINE_GRID = 2 };
 typedef struct {
     int32_t method;
@@ -133,7 +136,9 @@ void qtl_opts_default(qtl_opts* opts);
 
 /* Builds a system (paper Sec. 3.2 / 3.3 inputs: H, c_ops, e_ops) on the
  * current CUDA device.  The operators are copied; the caller may free them on
- * return.  All operators must have the same dimension n (1 <= n <= 46340).
+ * return.  All operators must have the same dimension n: 1 <= n <= 4,194,304
+ * for CSR operators, n <= 46340 for dense ones.  mesolve needs n <= 46340
+ * (QTL_ETOOBIG above); mcsolve takes the full range.
  * The library forms, in FP64 on the host:
  *   A = -i H - 1/2 sum_k C_k^dag C_k   (so -i H_eff psi = A psi, Sec. 3.3),
  *   B =  i H - 1/2 sum_k C_k^dag C_k,
@@ -212,7 +217,12 @@ qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb, const qtl_c
  *             channel, threshold, ...
  *   expect_out[n_e*nt]: the trajectory mean of <psi|O_k|psi>/<psi|psi>.
  *   traj_expect_out NULL, or [n_e*nt*ntraj] laid out [(k*nt + t)*ntraj + j].
- * Host pointers; returns when done. */
+ * Host pointers; returns when done.  Up to n = 1024 a trajectory's state
+ * stays in the registers of one CTA; larger n (up to 4,194,304) runs one
+ * 1024-thread CTA per trajectory with its state in a stream-ordered scratch
+ * buffer of about 13 * 16 * n bytes per resident CTA (one per SM), returning
+ * QTL_ENOMEM if that cannot be allocated.  Both give the same trajectories
+ * up to rounding order. */
 qtl_status qtl_mcsolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
                        int32_t ntraj, uint64_t seed, int64_t traj_offset, const qtl_opts* opts,
                        qtl_c128* expect_out, qtl_c128* traj_expect_out, qtl_stats* stats);

@@ -34,6 +34,27 @@ struct DevCsr {
     float2* v32 = nullptr;
 };
 
+// Sliced ELLPACK copy of A for the wide trajectory kernel: rows in slices of
+// 32 (one warp's rows), entry p of the slice's 32 rows stored contiguously,
+// so every load of a warp is one coalesced 128/256-byte access.  Each slice
+// keeps the [real-only | imaginary-only | complex] grouping of DevCsr, each
+// group padded to its longest row with zero entries (column = the row).
+// sl[s] = {scalar offset, complex offset, real width, imaginary width};
+// sl[nslices] holds the end offsets, so the complex width of slice s is
+// (sl[s+1].y - sl[s].y) / 32.
+struct DevSell {
+    int n = 0, nslices = 0;
+    int64_t ns = 0, nc = 0;
+    int idx16 = 0;           // column indices stored as uint16 (n <= 65536)
+    int4* sl = nullptr;
+    void* ci_s = nullptr;    // int32 or uint16 per entry
+    void* ci_c = nullptr;
+    double* vs64 = nullptr;  // real part (real-only group) or imaginary part
+    float* vs32 = nullptr;
+    double2* vc64 = nullptr;
+    float2* vc32 = nullptr;
+};
+
 // ---------------------------------------------------------------- system
 struct System {
     int n = 0, n_c = 0, n_e = 0;
@@ -48,6 +69,7 @@ struct System {
     DevCsr dC;            // all collapse operators stacked: rows k*n .. k*n+n-1
     DevCsr dO;            // all observables stacked: rows k*n .. k*n+n-1
     DevCsr dL;            // Liouvillian (built lazily)
+    DevSell sA;           // A in sliced ELLPACK (built lazily for n > 1024 mcsolve)
     std::vector<int32_t> L_rp;  // host copy of its row pointers (shared-memory sizing)
     double2* ew = nullptr;      // [n*n][n_e] trace weights (built with the Liouvillian)
     int32_t* cmap = nullptr;    // [n_c][n] column of C_c's entry in row i, -1 if none
@@ -153,6 +175,29 @@ struct McJob {
     long long max_steps;
     int fixed;
     int method;
+    // trajectories above the register-resident size (mc_wide.cu)
+    const int4* sl;        // A in sliced ELLPACK (DevSell)
+    int sidx16;
+    const void* sci_s;
+    const void* sci_c;
+    const double* svs64;
+    const float* svs32;
+    const double2* svc64;
+    const float2* svc32;
+    unsigned char* wscr;   // [grid][wstride] bytes of per-CTA state
+    size_t wstride;
+    int xsmem;             // stage inputs in shared memory (1) or in wscr (0)
+    int xbufs;             // stage-input buffers in shared memory (1 or 2)
+};
+
+// Launch plan of the wide trajectory kernel: grid, shared memory and the
+// per-CTA scratch it needs (allocated by the caller).
+struct McWidePlan {
+    int grid;
+    int xsmem, xbufs;
+    size_t smem;
+    size_t stride;         // bytes of scratch per CTA
+    size_t scratch_bytes;  // grid * stride
 };
 
 // kernels (launchers return cudaError_t of the launch)
@@ -170,6 +215,10 @@ int me_cluster_capacity();
 cudaError_t launch_me_grid(const MgJob& J, int precision, cudaStream_t st, int* grid_out);
 int me_grid_blocks(int precision);        // max L handled by the cluster kernel
 int mc_traj_capacity();           // max n handled by the trajectory kernel
+int mc_wide_capacity();           // max n handled by the wide trajectory kernel
+cudaError_t mc_wide_plan(const McJob& job, int precision, McWidePlan* plan);
+cudaError_t launch_mc_wide(const McJob& job, int precision, const McWidePlan& plan, void* scratch,
+                           cudaStream_t st);
 
 void count_launch(int k = 1);
 void set_cuda_error(cudaError_t e);

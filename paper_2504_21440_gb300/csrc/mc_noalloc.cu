@@ -80,7 +80,8 @@ extern "C" qtl_status qtl_mcsolve_noalloc(
     const qtl_c128* o_vals, const qtl_c128* psi0, const double* tlist, int32_t nt, int32_t ntraj,
     uint64_t seed, int64_t traj_offset, const qtl_opts* opts, qtl_c128* expect,
     qtl_device_info* info) {
-    if (n < 1 || n > mc_traj_capacity() || !a_row_ptr || a_nnz < 0 || a_nnz >= INT32_MAX ||
+    if (n > mc_traj_capacity()) return QTL_ETOOBIG;
+    if (n < 1 || !a_row_ptr || a_nnz < 0 || a_nnz >= INT32_MAX ||
         (a_nnz > 0 && (!a_col_idx || !a_vals)) || n_c < 0 || n_c > 64 || n_e < 0 || n_e > 64 ||
         (n_c > 0 && (!c_row_ptr || !c_col_idx || !c_vals)) ||
         (n_e > 0 && (!o_row_ptr || !o_col_idx || !o_vals || !expect)) || !psi0 || !tlist ||

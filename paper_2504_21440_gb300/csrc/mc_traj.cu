@@ -20,183 +20,11 @@
 // (warp shuffle tree, then warps in order), so a trajectory's result does not
 // depend on which CTA or batch it runs in.
 #include "internal.h"
-#include "rk.cuh"
+#include "mc_common.cuh"
 
 namespace qtl {
 
 constexpr int MC_TMAX = 256;
-
-template <bool MIXED>
-struct MPrec;
-template <>
-struct MPrec<false> {
-    using T = double;
-    using T2 = double2;
-};
-template <>
-struct MPrec<true> {
-    using T = float;
-    using T2 = float2;
-};
-
-__device__ __forceinline__ double2 to_d2_mc(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d2_mc(float2 v) { return make_double2(v.x, v.y); }
-template <class T2>
-__device__ __forceinline__ T2 from_d2_mc(double2 v);
-template <>
-__device__ __forceinline__ double2 from_d2_mc<double2>(double2 v) { return v; }
-template <>
-__device__ __forceinline__ float2 from_d2_mc<float2>(double2 v) {
-    return make_float2((float)v.x, (float)v.y);
-}
-
-// Values reduced at once: |psi|^2 and 2 per observable, or 1 per channel.
-__host__ __device__ __forceinline__ int mc_red_stride(int n_e, int n_c) {
-    int a = 2 + 2 * n_e;
-    return a > n_c ? a : n_c;
-}
-
-__device__ __forceinline__ float mc_warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double mc_warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-struct BlockReducer {
-    double* wred;  // [nw][rs]
-    double* out;   // [rs]
-    int rs, lane, warp, tid, nw;
-    __device__ void stage(int i, double v) {
-        v = mc_warp_sum(v);
-        if (lane == 0) wred[warp * rs + i] = v;
-    }
-    __device__ void finish(int nv) {
-        __syncthreads();
-        if (tid < nv) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += wred[w * rs + tid];
-            out[tid] = s;
-        }
-        __syncthreads();
-    }
-};
-
-// Philox4x32-10: ten rounds of the published round function; key bumped by
-// the Weyl constants between rounds.
-__device__ __forceinline__ double philox_uniform(unsigned long long seed, unsigned long long traj,
-                                                 unsigned draw) {
-    unsigned c0 = draw, c1 = (unsigned)traj, c2 = 0u, c3 = 0u;
-    unsigned k0 = (unsigned)(seed & 0xffffffffull), k1 = (unsigned)(seed >> 32);
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        unsigned lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-        unsigned lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-        unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-    }
-    unsigned long long x = ((unsigned long long)c1 << 20) | (unsigned long long)(c0 >> 12);
-    return ((double)x + 0.5) * 0x1p-52;
-}
-
-// Row r of a segmented CSR (real-only | imaginary-only | complex entries)
-// times x held in shared memory.
-template <class T2, class TV>
-__device__ __forceinline__ T2 mc_spmv_row(int r, const int4* __restrict__ seg,
-                                          const int32_t* __restrict__ ci,
-                                          const TV* __restrict__ v, const T2* x) {
-    const int4 sg = __ldg(seg + r);
-    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
-    int p = sg.x;
-    for (; p < sg.y; ++p) {
-        const decltype(T2::x) a = __ldg(&v[p].x);
-        const T2 xv = x[__ldg(ci + p)];
-        ax = fma(a, xv.x, ax);
-        ay = fma(a, xv.y, ay);
-    }
-    for (; p < sg.z; ++p) {
-        const decltype(T2::x) b = __ldg(&v[p].y);
-        const T2 xv = x[__ldg(ci + p)];
-        bx = fma(-b, xv.y, bx);
-        by = fma(b, xv.x, by);
-    }
-    for (; p < sg.w; ++p) {
-        const TV a = __ldg(v + p);
-        const T2 xv = x[__ldg(ci + p)];
-        ax = fma(a.x, xv.x, ax);
-        ay = fma(a.x, xv.y, ay);
-        bx = fma(-a.y, xv.y, bx);
-        by = fma(a.y, xv.x, by);
-    }
-    T2 acc;
-    acc.x = ax + bx;
-    acc.y = ay + by;
-    return acc;
-}
-
-// A's row from the CTA's shared-memory copy (rows packed in CTA order).
-template <class T2, class TV>
-__device__ __forceinline__ T2 mc_spmv_row_s(int r, const int4* __restrict__ s_seg,
-                                            const int32_t* __restrict__ s_ci,
-                                            const TV* __restrict__ s_v, const T2* x) {
-    const int4 sg = s_seg[r];
-    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
-    int p = sg.x;
-#pragma unroll 4
-    for (; p < sg.y; ++p) {
-        const decltype(T2::x) a = s_v[p].x;
-        const T2 xv = x[s_ci[p]];
-        ax = fma(a, xv.x, ax);
-        ay = fma(a, xv.y, ay);
-    }
-#pragma unroll 4
-    for (; p < sg.z; ++p) {
-        const decltype(T2::x) b = s_v[p].y;
-        const T2 xv = x[s_ci[p]];
-        bx = fma(-b, xv.y, bx);
-        by = fma(b, xv.x, by);
-    }
-#pragma unroll 2
-    for (; p < sg.w; ++p) {
-        const TV a = s_v[p];
-        const T2 xv = x[s_ci[p]];
-        ax = fma(a.x, xv.x, ax);
-        ay = fma(a.x, xv.y, ay);
-        bx = fma(-a.y, xv.y, bx);
-        by = fma(a.y, xv.x, by);
-    }
-    T2 acc;
-    acc.x = ax + bx;
-    acc.y = ay + by;
-    return acc;
-}
-
-enum { MC_STEP = 0, MC_REPEAT = 1, MC_DONE = 2 };
-
-// Control block broadcast by thread 0 (scalar control in one thread: GB300's
-// FP64 pipe is 1/64 rate, so no FP64 scalar work is replicated per thread).
-struct McCtl {
-    double coef[28];  // htry * a_sj (21, packed by stage), htry * e_j (7)
-    float coeff[28];  // the same, rounded to FP32 (mixed precision)
-    double inv;       // 1 / |C_k psi*| of the chosen channel
-    int action, land, accept, save, ch, rootgo, pub;
-    float wf[MC_TMAX / 32];
-    double wd[MC_TMAX / 32];
-};
-
-__host__ __device__ constexpr int mc_coef_a(int s, int j) { return s * (s - 1) / 2 + j; }
 
 template <bool MIXED, int RPT, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
@@ -386,7 +214,7 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                 }
                 if (!(t < t_target)) {
                     cb.action = MC_REPEAT;
-                    cb.save = idx++;
+                    cb.rsave = idx++;
                     return;
                 }
                 if (attempts >= J.max_steps) {
@@ -516,7 +344,7 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                 for (int m = 0; m < RPT; ++m)
                     if (own[m]) yd[row[m]] = y[m];
                 __syncthreads();
-                const double nn = save(cb.save);
+                const double nn = save(cb.rsave);
                 if (tid == 0) {
                     norm2 = nn;
                     next_action();

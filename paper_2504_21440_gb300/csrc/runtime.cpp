@@ -41,7 +41,11 @@ static bool finite_c(const qtl_c128& v) { return std::isfinite(v.re) && std::isf
 // Converts a qtl_op to a canonical CSR: columns sorted, duplicates summed,
 // exact zeros dropped.
 static qtl_status to_csr(const qtl_op* op, int n_expect, Csr& out) {
-    if (!op || op->n <= 0 || op->n > 46340 || (n_expect > 0 && op->n != n_expect)) return QTL_EINVAL;
+    // CSR operators up to the trajectory kernel's limit; dense ones (n*n
+    // values) and any mesolve up to n = 46340 (n*n < 2^31)
+    if (!op || op->n <= 0 || op->n > mc_wide_capacity() || (n_expect > 0 && op->n != n_expect))
+        return QTL_EINVAL;
+    if (!op->is_csr && op->n > 46340) return QTL_EINVAL;
     if (!op->vals) return QTL_EINVAL;
     const int n = op->n;
     out = Csr();
@@ -265,7 +269,116 @@ static void free_csr(DevCsr& d) {
     d = DevCsr();
 }
 
+// A in sliced ELLPACK (see DevSell), entries grouped and ordered as in
+// upload_csr.
+static qtl_status upload_sell(const Csr& m, DevSell& d) {
+    const int n = m.n, ns_ = (n + 31) / 32;
+    std::vector<int4> sl(ns_ + 1);
+    std::vector<int32_t> ci_s, ci_c;
+    std::vector<double> vs;
+    std::vector<double2> vc;
+    std::vector<std::pair<int32_t, int64_t>> order;
+    std::vector<std::vector<int64_t>> grp[3];
+    for (int g = 0; g < 3; ++g) grp[g].resize(32);
+    for (int s = 0; s < ns_; ++s) {
+        int w[3] = {0, 0, 0};
+        for (int l = 0; l < 32; ++l) {
+            const int r = s * 32 + l;
+            for (int g = 0; g < 3; ++g) grp[g][l].clear();
+            if (r >= n) continue;
+            for (int g = 0; g < 3; ++g) {
+                order.clear();
+                for (int64_t p = m.rp[r]; p < m.rp[r + 1]; ++p) {
+                    const bool re0 = m.re[p] == 0.0, im0 = m.im[p] == 0.0;
+                    if ((im0 ? 0 : (re0 ? 1 : 2)) == g) order.emplace_back(m.ci[p] ^ r, p);
+                }
+                std::sort(order.begin(), order.end());
+                for (const auto& kp : order) grp[g][l].push_back(kp.second);
+                w[g] = std::max(w[g], (int)grp[g][l].size());
+            }
+        }
+        sl[s] = make_int4((int)ci_s.size(), (int)ci_c.size(), w[0], w[1]);
+        for (int g = 0; g < 2; ++g)
+            for (int p = 0; p < w[g]; ++p)
+                for (int l = 0; l < 32; ++l) {
+                    const int r = std::min(s * 32 + l, n - 1);
+                    if (p < (int)grp[g][l].size()) {
+                        const int64_t e = grp[g][l][p];
+                        ci_s.push_back(m.ci[e]);
+                        vs.push_back(g == 0 ? m.re[e] : m.im[e]);
+                    } else {
+                        ci_s.push_back(r);
+                        vs.push_back(0.0);
+                    }
+                }
+        for (int p = 0; p < w[2]; ++p)
+            for (int l = 0; l < 32; ++l) {
+                const int r = std::min(s * 32 + l, n - 1);
+                if (p < (int)grp[2][l].size()) {
+                    const int64_t e = grp[2][l][p];
+                    ci_c.push_back(m.ci[e]);
+                    vc.push_back(make_double2(m.re[e], m.im[e]));
+                } else {
+                    ci_c.push_back(r);
+                    vc.push_back(make_double2(0.0, 0.0));
+                }
+            }
+        if (ci_s.size() >= (size_t)INT32_MAX || ci_c.size() >= (size_t)INT32_MAX) return QTL_ETOOBIG;
+    }
+    sl[ns_] = make_int4((int)ci_s.size(), (int)ci_c.size(), 0, 0);
+    std::vector<float> vs32(vs.size());
+    std::vector<float2> vc32(vc.size());
+    for (size_t i = 0; i < vs.size(); ++i) vs32[i] = (float)vs[i];
+    for (size_t i = 0; i < vc.size(); ++i) vc32[i] = make_float2((float)vc[i].x, (float)vc[i].y);
+    d.n = n;
+    d.nslices = ns_;
+    d.ns = (int64_t)vs.size();
+    d.nc = (int64_t)vc.size();
+    d.idx16 = n <= 65536;
+    qtl_status st;
+    if ((st = upload(&d.sl, sl.data(), sl.size())) != QTL_OK) return st;
+    if (d.idx16) {
+        // half the index traffic: columns fit in 16 bits
+        std::vector<uint16_t> s16(ci_s.begin(), ci_s.end()), c16(ci_c.begin(), ci_c.end());
+        uint16_t *ds = nullptr, *dc = nullptr;
+        if ((st = upload(&ds, s16.data(), s16.size())) != QTL_OK) return st;
+        d.ci_s = ds;
+        if ((st = upload(&dc, c16.data(), c16.size())) != QTL_OK) return st;
+        d.ci_c = dc;
+    } else {
+        int32_t *ds = nullptr, *dc = nullptr;
+        if ((st = upload(&ds, ci_s.data(), ci_s.size())) != QTL_OK) return st;
+        d.ci_s = ds;
+        if ((st = upload(&dc, ci_c.data(), ci_c.size())) != QTL_OK) return st;
+        d.ci_c = dc;
+    }
+    if ((st = upload(&d.vs64, vs.data(), vs.size())) != QTL_OK) return st;
+    if ((st = upload(&d.vs32, vs32.data(), vs32.size())) != QTL_OK) return st;
+    if ((st = upload(&d.vc64, vc.data(), vc.size())) != QTL_OK) return st;
+    if ((st = upload(&d.vc32, vc32.data(), vc32.size())) != QTL_OK) return st;
+    return QTL_OK;
+}
+
+static void free_sell(DevSell& d) {
+    cudaFree(d.sl);
+    cudaFree(d.ci_s);
+    cudaFree(d.ci_c);
+    cudaFree(d.vs64);
+    cudaFree(d.vs32);
+    cudaFree(d.vc64);
+    cudaFree(d.vc32);
+    d = DevSell();
+}
+
 static std::mutex g_build_mu;
+
+static qtl_status ensure_sell(System& s) {
+    std::lock_guard<std::mutex> lk(g_build_mu);
+    if (s.sA.sl) return QTL_OK;
+    qtl_status st = upload_sell(s.A, s.sA);
+    if (st != QTL_OK) free_sell(s.sA);
+    return st;
+}
 
 static qtl_status ensure_liouvillian(System& s) {
     std::lock_guard<std::mutex> lk(g_build_mu);
@@ -456,6 +569,7 @@ void qtl_system_free(qtl_system* sys) {
     free_csr(s.dC);
     free_csr(s.dO);
     free_csr(s.dL);
+    free_sell(s.sA);
     cudaFree(s.ew);
     delete sys;
 }
@@ -547,6 +661,7 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     qtl_status st = check_opts(opts);
     if (st != QTL_OK) return st;
     System& s = sys->s;
+    if (s.n > 46340) return QTL_ETOOBIG;
     {
         // engine: the cluster kernel when the problem fits one cluster
         const int64_t L64 = (int64_t)s.n * s.n;
@@ -925,7 +1040,9 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     if (st != QTL_OK) return st;
     System& s = sys->s;
     if (s.n_e > 0 && !expect_dev) return QTL_EINVAL;
-    if (s.n > mc_traj_capacity()) return QTL_ETOOBIG;
+    if (s.n > mc_wide_capacity()) return QTL_ETOOBIG;
+    if (opts->engine == QTL_ENGINE_CLUSTER && s.n > mc_traj_capacity()) return QTL_ETOOBIG;
+    const bool wide = s.n > mc_traj_capacity() || opts->engine == QTL_ENGINE_GRID;
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     const size_t ne = (size_t)s.n_e * nt;
     double2* scratch = nullptr;
@@ -967,7 +1084,34 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     J.fixed = opts->fixed_step ? 1 : 0;
     J.method = opts->method;
     QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
-    cudaError_t e = launch_mc_traj(J, opts->precision, stream);
+    cudaError_t e = cudaSuccess;
+    if (wide) {
+        // per-CTA integrator state in global memory (psi does not fit on chip)
+        if ((st = ensure_sell(s)) != QTL_OK) {
+            if (scratch) cudaFreeAsync(scratch, stream);
+            return st;
+        }
+        J.sl = s.sA.sl;
+        J.sidx16 = s.sA.idx16;
+        J.sci_s = s.sA.ci_s;
+        J.sci_c = s.sA.ci_c;
+        J.svs64 = s.sA.vs64;
+        J.svs32 = s.sA.vs32;
+        J.svc64 = s.sA.vc64;
+        J.svc32 = s.sA.vc32;
+        McWidePlan plan;
+        void* wscr = nullptr;
+        e = mc_wide_plan(J, opts->precision, &plan);
+        if (e == cudaSuccess && cudaMallocAsync(&wscr, plan.scratch_bytes, stream) != cudaSuccess) {
+            cudaGetLastError();
+            if (scratch) cudaFreeAsync(scratch, stream);
+            return QTL_ENOMEM;
+        }
+        if (e == cudaSuccess) e = launch_mc_wide(J, opts->precision, plan, wscr, stream);
+        if (wscr) cudaFreeAsync(wscr, stream);
+    } else {
+        e = launch_mc_traj(J, opts->precision, stream);
+    }
     if (e == cudaSuccess) e = launch_mc_reduce(J, stream);
     if (scratch) cudaFreeAsync(scratch, stream);
     if (e != cudaSuccess) {

@@ -73,6 +73,16 @@ static size_t request_bytes(const qtl_request& r) {
     size_t b = (r.is_ket || r.kind == QTL_REQ_MCSOLVE ? n : L) * 16 + nt * 8 + ne * nt * 16 + 4096;
     if (r.kind == QTL_REQ_MCSOLVE) {
         b += ne * nt * (size_t)r.ntraj * 16;
+        if (s.n > mc_traj_capacity()) {
+            McJob J{};
+            J.n = s.n;
+            J.n_e = s.n_e;
+            J.n_c = s.n_c;
+            J.ntraj = r.ntraj;
+            McWidePlan p{};
+            if (mc_wide_plan(J, r.opts.precision, &p) == cudaSuccess) b += p.scratch_bytes;
+            else b += (size_t)r.ntraj * 15 * n * 16;
+        }
     } else if (L <= (size_t)me_cluster_capacity() && r.opts.engine != QTL_ENGINE_GRID) {
         b += nt * 16 * 2 * ne * 8 + L * 40;  // expectation partials; Liouvillian if built here
     } else {

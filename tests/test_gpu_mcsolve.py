@@ -91,6 +91,18 @@ def test_mixed_precision_trajectories():
         assert maxabs(got["traj_expect"][j], ref["traj_expect"][j]) <= 1e-5
 
 
+def test_repeated_output_times():
+    """A time listed twice is saved twice: the landing step saves the first
+    copy and the repeat the second."""
+    s = W.jaynes_cummings(N=4, nt=11, t_end=40.0, kappa=0.2)
+    tl = np.array([0.0, 5.0, 5.0, 12.0, 12.0, 12.0, 20.0])
+    ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, tl, ntraj=6, seed=8,
+                         keep_trajectories=True)
+    got = _gpu(s, tl, 6, 8)
+    assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-8
+    assert maxabs(got["traj_expect"][:, :, 1], got["traj_expect"][:, :, 2]) == 0.0
+
+
 def test_mcsolve_edge_cases():
     qtl = require_gpu()
     s = W.two_level_decay()
