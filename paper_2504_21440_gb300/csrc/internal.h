@@ -34,25 +34,50 @@ struct DevCsr {
     float2* v32 = nullptr;
 };
 
-// Sliced ELLPACK copy of A for the wide trajectory kernel: rows in slices of
-// 32 (one warp's rows), entry p of the slice's 32 rows stored contiguously,
-// so every load of a warp is one coalesced 128/256-byte access.  Each slice
-// keeps the [real-only | imaginary-only | complex] grouping of DevCsr, each
-// group padded to its longest row with zero entries (column = the row).
-// sl[s] = {scalar offset, complex offset, real width, imaginary width};
-// sl[nslices] holds the end offsets, so the complex width of slice s is
-// (sl[s+1].y - sl[s].y) / 32.
+// Sliced ELLPACK copy of A for the wide trajectory kernel, with the
+// structure of tensor-product operators factored out.  Rows come in slices of
+// 32 (one warp's rows); each row's entries are grouped real-only |
+// imaginary-only | complex as in DevCsr and ordered by col XOR row, and each
+// group is padded to the slice's longest row.  Entry position p of a slice
+// is described by {mode, column parameter, value index, 0}:
+//   column: explicit (ci[cbase + param + lane]), XOR (row ^ param: Pauli-type
+//           flips) or offset (row + param: ladder-type shifts), whichever
+//           holds for all 32 rows (padding rows only need an in-range column);
+//   value:  uniform (vs[param'] / vc[param'], one value shared by the 32
+//           rows, stored once for the whole operator) or explicit
+//           (vs[vsbase + param' + lane] / vc[vcbase + param' + lane]);
+//           padding entries are zeros.
+// Explicit parts are addressed relative to the slice's bases, so slices with
+// the same pattern share one descriptor list: for the Ising chain all 512
+// slices of the 14-spin operator use the same 15 descriptors (L1-resident),
+// and the only per-row data left is the diagonal.
+// Descriptor .w holds the FP32 bits of a uniform real or imaginary value.
+// sl[2s] = {first descriptor, real, imaginary, complex widths},
+// sl[2s+1] = {cbase, vsbase, vcbase, group types}.
+enum { SELL_COL_EXPLICIT = 0, SELL_COL_XOR = 1, SELL_COL_OFFSET = 2, SELL_VAL_UNIFORM = 4 };
+// Per-slice group types (sl[2s+1].w, 2 bits per group, real | imaginary |
+// complex), each run by its own loop in the kernel.
+enum { SELL_G_GENERAL = 0, SELL_G_XU = 1, SELL_G_XE = 2, SELL_G_EE = 3 };
 struct DevSell {
     int n = 0, nslices = 0;
-    int64_t ns = 0, nc = 0;
-    int idx16 = 0;           // column indices stored as uint16 (n <= 65536)
-    int4* sl = nullptr;
-    void* ci_s = nullptr;    // int32 or uint16 per entry
-    void* ci_c = nullptr;
-    double* vs64 = nullptr;  // real part (real-only group) or imaginary part
+    int idx16 = 0;           // explicit columns stored as uint16 (n <= 65536)
+    int64_t ndesc = 0, nci = 0, nvs = 0, nvc = 0;
+    int4* sl = nullptr;      // [2 nslices]
+    int4* desc = nullptr;    // [ndesc] shared descriptor lists
+    void* ci = nullptr;      // [nci] explicit columns, 32 per explicit descriptor
+    double* vs64 = nullptr;  // [nvs] real part (real-only group) or imaginary part
     float* vs32 = nullptr;
-    double2* vc64 = nullptr;
+    double2* vc64 = nullptr; // [nvc] complex values
     float2* vc32 = nullptr;
+    std::vector<int4> hdesc; // host copy of the descriptors when there are few
+};
+
+// Descriptors passed to the wide kernel as a __grid_constant__ parameter
+// when they fit: the loads then go through the constant cache and leave the
+// L1 data pipe to the stage-input gathers.
+constexpr int SELL_CDESC = 256;
+struct SellConst {
+    int4 d[SELL_CDESC];
 };
 
 // ---------------------------------------------------------------- system
@@ -162,6 +187,7 @@ struct McJob {
     const int32_t* orp;   // stacked observables
     const int32_t* oci;
     const double2* ov;
+    const int4* oseg;     // their row segments (real-only | imaginary-only | complex), or null
     const double* tlist;
     int nt;
     const double2* psi0;
@@ -176,10 +202,11 @@ struct McJob {
     int fixed;
     int method;
     // trajectories above the register-resident size (mc_wide.cu)
-    const int4* sl;        // A in sliced ELLPACK (DevSell)
+    const int4* sl;        // A in pattern-compressed sliced ELLPACK (DevSell)
+    const int4* sdesc;
+    int sdesc_const;       // 1: the descriptors are in the kernel's SellConst parameter
     int sidx16;
-    const void* sci_s;
-    const void* sci_c;
+    const void* sci;
     const double* svs64;
     const float* svs32;
     const double2* svc64;
@@ -218,7 +245,7 @@ int mc_traj_capacity();           // max n handled by the trajectory kernel
 int mc_wide_capacity();           // max n handled by the wide trajectory kernel
 cudaError_t mc_wide_plan(const McJob& job, int precision, McWidePlan* plan);
 cudaError_t launch_mc_wide(const McJob& job, int precision, const McWidePlan& plan, void* scratch,
-                           cudaStream_t st);
+                           const SellConst* cdesc, cudaStream_t st);
 
 void count_launch(int k = 1);
 void set_cuda_error(cudaError_t e);

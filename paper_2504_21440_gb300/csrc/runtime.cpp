@@ -3,6 +3,7 @@
 // B^T and the column-stacking Liouvillian (paper Sec. 3.2 / 3.3), device
 // uploads, and the mesolve / mcsolve drivers that enqueue the kernels.
 #include <algorithm>
+#include <map>
 #include <atomic>
 #include <cmath>
 #include <complex>
@@ -269,23 +270,27 @@ static void free_csr(DevCsr& d) {
     d = DevCsr();
 }
 
-// A in sliced ELLPACK (see DevSell), entries grouped and ordered as in
-// upload_csr.
+// A in pattern-compressed sliced ELLPACK (see DevSell); entries grouped and
+// ordered as in upload_csr.  Descriptor lists and uniform values are
+// deduplicated across slices.
 static qtl_status upload_sell(const Csr& m, DevSell& d) {
     const int n = m.n, ns_ = (n + 31) / 32;
-    std::vector<int4> sl(ns_ + 1);
-    std::vector<int32_t> ci_s, ci_c;
+    std::vector<int4> sl(2 * (size_t)ns_), desc, list;
+    std::vector<int32_t> ci;
     std::vector<double> vs;
     std::vector<double2> vc;
+    std::map<std::vector<int64_t>, int> lists;         // descriptor list -> first descriptor
+    std::map<std::pair<double, double>, int> uni_s, uni_c;  // uniform value -> index
     std::vector<std::pair<int32_t, int64_t>> order;
     std::vector<std::vector<int64_t>> grp[3];
     for (int g = 0; g < 3; ++g) grp[g].resize(32);
     for (int s = 0; s < ns_; ++s) {
         int w[3] = {0, 0, 0};
+        const int r0 = s * 32, nl = std::min(32, n - r0);  // valid rows of the slice
         for (int l = 0; l < 32; ++l) {
-            const int r = s * 32 + l;
             for (int g = 0; g < 3; ++g) grp[g][l].clear();
-            if (r >= n) continue;
+            if (l >= nl) continue;
+            const int r = r0 + l;
             for (int g = 0; g < 3; ++g) {
                 order.clear();
                 for (int64_t p = m.rp[r]; p < m.rp[r + 1]; ++p) {
@@ -297,60 +302,182 @@ static qtl_status upload_sell(const Csr& m, DevSell& d) {
                 w[g] = std::max(w[g], (int)grp[g][l].size());
             }
         }
-        sl[s] = make_int4((int)ci_s.size(), (int)ci_c.size(), w[0], w[1]);
-        for (int g = 0; g < 2; ++g)
-            for (int p = 0; p < w[g]; ++p)
-                for (int l = 0; l < 32; ++l) {
-                    const int r = std::min(s * 32 + l, n - 1);
-                    if (p < (int)grp[g][l].size()) {
-                        const int64_t e = grp[g][l][p];
-                        ci_s.push_back(m.ci[e]);
-                        vs.push_back(g == 0 ? m.re[e] : m.im[e]);
-                    } else {
-                        ci_s.push_back(r);
-                        vs.push_back(0.0);
+        const int cbase = (int)ci.size(), vsbase = (int)vs.size(), vcbase = (int)vc.size();
+        list.clear();
+        for (int g = 0; g < 3; ++g)
+            for (int p = 0; p < w[g]; ++p) {
+                // entry of lane l at position p, or -1 (padding)
+                auto ent = [&](int l) -> int64_t {
+                    return p < (int)grp[g][l].size() ? grp[g][l][p] : -1;
+                };
+                // column pattern: XOR, then offset, else explicit; a padding
+                // lane accepts any pattern whose column is in range
+                int mode = SELL_COL_EXPLICIT, param = 0;
+                for (int cand = SELL_COL_XOR; cand <= SELL_COL_OFFSET && mode == SELL_COL_EXPLICIT; ++cand) {
+                    bool have = false, ok = true;
+                    int64_t pv = 0;
+                    for (int l = 0; l < nl && ok; ++l) {
+                        const int64_t e = ent(l);
+                        if (e < 0) continue;
+                        const int r = r0 + l, c = m.ci[e];
+                        const int64_t v = cand == SELL_COL_XOR ? (int64_t)(c ^ r) : (int64_t)c - r;
+                        if (!have) {
+                            pv = v;
+                            have = true;
+                        } else if (v != pv) {
+                            ok = false;
+                        }
+                    }
+                    if (!have || !ok) continue;
+                    for (int l = 0; l < nl && ok; ++l) {
+                        if (ent(l) >= 0) continue;
+                        const int64_t r = r0 + l;
+                        const int64_t c = cand == SELL_COL_XOR ? (r ^ pv) : r + pv;
+                        ok = c >= 0 && c < n;
+                    }
+                    if (ok) {
+                        mode = cand;
+                        param = (int)pv;
                     }
                 }
-        for (int p = 0; p < w[2]; ++p)
-            for (int l = 0; l < 32; ++l) {
-                const int r = std::min(s * 32 + l, n - 1);
-                if (p < (int)grp[2][l].size()) {
-                    const int64_t e = grp[2][l][p];
-                    ci_c.push_back(m.ci[e]);
-                    vc.push_back(make_double2(m.re[e], m.im[e]));
-                } else {
-                    ci_c.push_back(r);
-                    vc.push_back(make_double2(0.0, 0.0));
+                if (mode == SELL_COL_EXPLICIT) {
+                    param = (int)ci.size() - cbase;
+                    for (int l = 0; l < 32; ++l) {
+                        const int64_t e = l < nl ? ent(l) : -1;
+                        ci.push_back(e >= 0 ? m.ci[e] : std::min(r0 + l, n - 1));
+                    }
                 }
+                // values: uniform when every valid lane holds the same entry value
+                bool uni = true;
+                const int64_t e0 = ent(0);
+                for (int l = 0; l < nl && uni; ++l) {
+                    const int64_t e = ent(l);
+                    if (e < 0 || e0 < 0 || m.re[e] != m.re[e0] || m.im[e] != m.im[e0]) uni = false;
+                }
+                int vix;
+                if (uni) {
+                    const std::pair<double, double> key(m.re[e0], m.im[e0]);
+                    auto& tab = g < 2 ? uni_s : uni_c;
+                    auto it = tab.find(key);
+                    if (it != tab.end()) {
+                        vix = it->second;
+                    } else {
+                        if (g < 2) {
+                            vix = (int)vs.size();
+                            vs.push_back(g == 0 ? m.re[e0] : m.im[e0]);
+                        } else {
+                            vix = (int)vc.size();
+                            vc.push_back(make_double2(m.re[e0], m.im[e0]));
+                        }
+                        tab.emplace(key, vix);
+                    }
+                } else if (g < 2) {
+                    vix = (int)vs.size() - vsbase;
+                    for (int l = 0; l < 32; ++l) {
+                        const int64_t e = l < nl ? ent(l) : -1;
+                        vs.push_back(e < 0 ? 0.0 : (g == 0 ? m.re[e] : m.im[e]));
+                    }
+                } else {
+                    vix = (int)vc.size() - vcbase;
+                    for (int l = 0; l < 32; ++l) {
+                        const int64_t e = l < nl ? ent(l) : -1;
+                        vc.push_back(e < 0 ? make_double2(0.0, 0.0) : make_double2(m.re[e], m.im[e]));
+                    }
+                }
+                // .w: the FP32 bits of a uniform real or imaginary value
+                int f32 = 0;
+                if (uni && g < 2) {
+                    const float f = (float)(g == 0 ? m.re[e0] : m.im[e0]);
+                    std::memcpy(&f32, &f, 4);
+                }
+                list.push_back(make_int4(mode | (uni ? SELL_VAL_UNIFORM : 0), param, vix, f32));
             }
-        if (ci_s.size() >= (size_t)INT32_MAX || ci_c.size() >= (size_t)INT32_MAX) return QTL_ETOOBIG;
+        // group types (2 bits each): XOR columns with uniform values, XOR
+        // columns with explicit values, explicit columns and values, or
+        // mixed modes; explicit blocks of a typed group are contiguous
+        // (32 entries apart), so the kernel needs only the group's first
+        // descriptor for them
+        int types = 0;
+        {
+            int off = 0;
+            for (int g = 0; g < 3; ++g) {
+                int ty = SELL_G_GENERAL;
+                if (w[g] > 0) {
+                    bool xu = true, xe = true, ee = true;
+                    for (int p = 0; p < w[g]; ++p) {
+                        const int4& q = list[off + p];
+                        const int cm = q.x & 3;
+                        const bool un = (q.x & SELL_VAL_UNIFORM) != 0;
+                        const int4& q0 = list[off];
+                        xu = xu && cm == SELL_COL_XOR && un;
+                        xe = xe && cm == SELL_COL_XOR && !un && q.z == q0.z + 32 * p;
+                        ee = ee && cm == SELL_COL_EXPLICIT && !un && q.z == q0.z + 32 * p &&
+                             q.y == q0.y + 32 * p;
+                    }
+                    ty = xu ? SELL_G_XU : (xe ? SELL_G_XE : (ee ? SELL_G_EE : SELL_G_GENERAL));
+                }
+                types |= ty << (2 * g);
+                off += w[g];
+            }
+        }
+        // Explicit offsets are relative to the slice's bases; a uniform value
+        // first seen inside a slice shifts them, so that slice's list is
+        // stored separately, and from then on equal patterns share a list.
+        std::vector<int64_t> key;
+        key.reserve(list.size() * 3 + 3);
+        key.push_back(w[0]);
+        key.push_back(w[1]);
+        key.push_back(w[2]);
+        for (const int4& q : list) {
+            key.push_back(q.x);
+            key.push_back(q.y);
+            key.push_back(q.z);
+        }
+        auto it = lists.find(key);
+        int first;
+        if (it != lists.end()) {
+            first = it->second;
+        } else {
+            first = (int)desc.size();
+            desc.insert(desc.end(), list.begin(), list.end());
+            lists.emplace(std::move(key), first);
+        }
+        sl[2 * (size_t)s] = make_int4(first, w[0], w[1], w[2]);
+        sl[2 * (size_t)s + 1] = make_int4(cbase, vsbase, vcbase, types);
+        if (desc.size() >= (size_t)INT32_MAX || ci.size() >= (size_t)INT32_MAX ||
+            vs.size() >= (size_t)INT32_MAX || vc.size() >= (size_t)INT32_MAX)
+            return QTL_ETOOBIG;
     }
-    sl[ns_] = make_int4((int)ci_s.size(), (int)ci_c.size(), 0, 0);
+    // keep every array non-empty so that the device pointers are valid
+    if (ci.empty()) ci.push_back(0);
+    if (vs.empty()) vs.push_back(0.0);
+    if (vc.empty()) vc.push_back(make_double2(0.0, 0.0));
+    if (desc.empty()) desc.push_back(make_int4(0, 0, 0, 0));
     std::vector<float> vs32(vs.size());
     std::vector<float2> vc32(vc.size());
     for (size_t i = 0; i < vs.size(); ++i) vs32[i] = (float)vs[i];
     for (size_t i = 0; i < vc.size(); ++i) vc32[i] = make_float2((float)vc[i].x, (float)vc[i].y);
     d.n = n;
     d.nslices = ns_;
-    d.ns = (int64_t)vs.size();
-    d.nc = (int64_t)vc.size();
-    d.idx16 = n <= 65536;
+    d.ndesc = (int64_t)desc.size();
+    d.nci = (int64_t)ci.size();
+    d.nvs = (int64_t)vs.size();
+    d.nvc = (int64_t)vc.size();
+    d.idx16 = 0;
     qtl_status st;
+    if (desc.size() <= (size_t)SELL_CDESC) d.hdesc = desc;
     if ((st = upload(&d.sl, sl.data(), sl.size())) != QTL_OK) return st;
+    if ((st = upload(&d.desc, desc.data(), desc.size())) != QTL_OK) return st;
     if (d.idx16) {
         // half the index traffic: columns fit in 16 bits
-        std::vector<uint16_t> s16(ci_s.begin(), ci_s.end()), c16(ci_c.begin(), ci_c.end());
-        uint16_t *ds = nullptr, *dc = nullptr;
-        if ((st = upload(&ds, s16.data(), s16.size())) != QTL_OK) return st;
-        d.ci_s = ds;
+        std::vector<uint16_t> c16(ci.begin(), ci.end());
+        uint16_t* dc = nullptr;
         if ((st = upload(&dc, c16.data(), c16.size())) != QTL_OK) return st;
-        d.ci_c = dc;
+        d.ci = dc;
     } else {
-        int32_t *ds = nullptr, *dc = nullptr;
-        if ((st = upload(&ds, ci_s.data(), ci_s.size())) != QTL_OK) return st;
-        d.ci_s = ds;
-        if ((st = upload(&dc, ci_c.data(), ci_c.size())) != QTL_OK) return st;
-        d.ci_c = dc;
+        int32_t* dc = nullptr;
+        if ((st = upload(&dc, ci.data(), ci.size())) != QTL_OK) return st;
+        d.ci = dc;
     }
     if ((st = upload(&d.vs64, vs.data(), vs.size())) != QTL_OK) return st;
     if ((st = upload(&d.vs32, vs32.data(), vs32.size())) != QTL_OK) return st;
@@ -361,8 +488,8 @@ static qtl_status upload_sell(const Csr& m, DevSell& d) {
 
 static void free_sell(DevSell& d) {
     cudaFree(d.sl);
-    cudaFree(d.ci_s);
-    cudaFree(d.ci_c);
+    cudaFree(d.desc);
+    cudaFree(d.ci);
     cudaFree(d.vs64);
     cudaFree(d.vs32);
     cudaFree(d.vc64);
@@ -1066,6 +1193,7 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     J.orp = s.dO.rp;
     J.oci = s.dO.ci;
     J.ov = s.dO.v64;
+    J.oseg = s.dO.seg;
     J.tlist = tlist_dev;
     J.nt = nt;
     J.psi0 = (const double2*)psi0_dev;
@@ -1092,9 +1220,13 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
             return st;
         }
         J.sl = s.sA.sl;
+        J.sdesc = s.sA.desc;
+        SellConst cdesc;
+        std::memset(&cdesc, 0, sizeof(cdesc));
+        J.sdesc_const = !s.sA.hdesc.empty();
+        if (J.sdesc_const) std::memcpy(cdesc.d, s.sA.hdesc.data(), s.sA.hdesc.size() * sizeof(int4));
         J.sidx16 = s.sA.idx16;
-        J.sci_s = s.sA.ci_s;
-        J.sci_c = s.sA.ci_c;
+        J.sci = s.sA.ci;
         J.svs64 = s.sA.vs64;
         J.svs32 = s.sA.vs32;
         J.svc64 = s.sA.vc64;
@@ -1107,7 +1239,7 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
             if (scratch) cudaFreeAsync(scratch, stream);
             return QTL_ENOMEM;
         }
-        if (e == cudaSuccess) e = launch_mc_wide(J, opts->precision, plan, wscr, stream);
+        if (e == cudaSuccess) e = launch_mc_wide(J, opts->precision, plan, wscr, &cdesc, stream);
         if (wscr) cudaFreeAsync(wscr, stream);
     } else {
         e = launch_mc_traj(J, opts->precision, stream);
