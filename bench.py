@@ -548,7 +548,7 @@ def run_ising14_mc(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = 320.0 * s.n * statistics.mean(atts) / (mean_ms / 1e3) / 1e9
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", "mc_wide.cu"),
+    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", "mc_wide.cuh"),
                                    os.path.join(ROOT, "profiles", "mc_wide_kernel_ising14_mixed.md"))
     print(json.dumps({
         "metric": "mcsolve traj/s (14-spin Ising, n = 16384, 2000 trajectories)",
