@@ -94,7 +94,12 @@ struct System {
     DevCsr dC;            // all collapse operators stacked: rows k*n .. k*n+n-1
     DevCsr dO;            // all observables stacked: rows k*n .. k*n+n-1
     DevCsr dL;            // Liouvillian (built lazily)
-    DevSell sA;           // A in sliced ELLPACK (built lazily for n > 1024 mcsolve)
+    DevSell sA;           // A in sliced ELLPACK (built lazily: wide trajectories, grid mesolve)
+    DevSell sBt;          // B^T in sliced ELLPACK (built lazily: grid mesolve)
+    int2* units = nullptr;      // grid-mesolve work units (built with sBt)
+    int nu_tri = 0, nu_all = 0;
+    int herm_h = 0;             // H == H^dag exactly
+    int c_real = 0;             // every collapse-operator value is real
     std::vector<int32_t> L_rp;  // host copy of its row pointers (shared-memory sizing)
     double2* ew = nullptr;      // [n*n][n_e] trace weights (built with the Liouvillian)
     int32_t* cmap = nullptr;    // [n_c][n] column of C_c's entry in row i, -1 if none
@@ -127,18 +132,28 @@ struct MeJob {
     int smem_nnz;         // per-CTA shared-memory capacity for Liouvillian entries
 };
 
+// One operator in pattern-compressed sliced ELLPACK, as the kernels read it.
+struct SellRef {
+    const int4* sl;       // [2 nslices]
+    const int4* desc;
+    const int32_t* ci;
+    const double* vs64;
+    const float* vs32;
+    const double2* vc64;
+    const float2* vc32;
+};
+
 // Large-rho mesolve (one cooperative grid per solve, product-form RHS).
 struct MgJob {
     int n;
     long long L;
-    const int4* aseg;     // A, segmented rows
-    const int32_t* aci;
-    const double2* av64;
-    const float2* av32;
-    const int4* bseg;     // B^T, segmented rows
-    const int32_t* bci;
-    const double2* bv64;
-    const float2* bv32;
+    SellRef a;            // A = -i H - 1/2 sum C^dag C
+    SellRef bt;           // B^T, B = i H - 1/2 sum C^dag C
+    const int2* units;    // warp work units {row slice, column group}; the
+                          // units meeting the lower triangle come first
+    int nu_tri, nu_all;
+    int herm_h;           // H is exactly Hermitian
+    int c_real;           // every collapse-operator value is real (cmap path)
     int n_c;
     const int32_t* crp;   // collapse operators stacked row-wise (plain CSR)
     const int32_t* cci;
@@ -159,6 +174,9 @@ struct MgJob {
     double2* y1buf;
     void* k;              // scratch [7][L] stage derivatives (FP64 or FP32)
     void* ys;             // scratch [2][L] stage inputs (FP64 or FP32)
+    float4* base;         // MIXED: scratch [2][L] derivative at y as an FP32 pair (current, candidate)
+    double2* y64;         // MIXED: scratch [L] FP64 stage input of the FP64 base evaluation
+    int refresh;          // MIXED: accepted steps between FP64 evaluations of the base
     float* errpart;       // scratch [grid] error partials
     double* epart;        // scratch [nt][grid][2 n_e] expectation partials
     double2* expect;      // [n_e*nt]

@@ -12,6 +12,16 @@ from tests.gpu_util import maxabs, require_gpu
 pytestmark = pytest.mark.gpu
 
 
+def _gpu_state(s, state0, tlist, **kw):
+    qtl = require_gpu()
+    save = kw.pop("save_states", False)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    try:
+        return g.mesolve(state0, tlist, save_states=save, engine="grid", **kw)
+    finally:
+        g.free()
+
+
 def _gpu(s, tlist, **kw):
     qtl = require_gpu()
     save = kw.pop("save_states", False)
@@ -81,3 +91,69 @@ def test_ising10_h0_closed_form_mixed_adaptive():
     ref = 10 * (2 * np.exp(-0.1 * s.tlist) - 1)
     assert np.max(np.abs(got["expect"][2].real - ref)) <= 1e-5
     assert np.max(np.abs(got["expect"][0])) <= 1e-6   # Sx stays 0
+
+
+@pytest.mark.parametrize("N", [37, 45, 66])
+def test_grid_ragged_sizes_fixed_steps(N):
+    """Dimensions that are not multiples of the 32-row slices or the 4-column
+    work units (partial slices and column groups) against the oracle."""
+    s = W.driven_cavity(N=N)
+    tl = np.linspace(0, 0.5, 3)
+    ref = oracle_mesolve(s.H, s.c_ops, s.e_ops, s.psi0, tl, fixed_dt=0.01, save_states=True,
+                         rhs="product")
+    got = _gpu(s, tl, fixed_dt=0.01, save_states=True)
+    assert maxabs(got["expect"], ref["expect"]) <= 1e-10
+    assert maxabs(got["states"], ref["states"]) <= 1e-10
+
+
+def test_grid_non_hermitian_rho0_full_mode():
+    """A non-Hermitian initial matrix (the kernel then integrates every entry,
+    not the lower triangle) against the oracle, entry by entry."""
+    s = W.jaynes_cummings(N=10)
+    n = s.H.shape[0]
+    rng = np.random.default_rng(11)
+    rho0 = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    tl = np.linspace(0, 1.0, 3)
+    ref = oracle_mesolve(s.H, s.c_ops, s.e_ops, rho0, tl, fixed_dt=0.02, save_states=True,
+                         rhs="product")
+    got = _gpu_state(s, rho0, tl, fixed_dt=0.02, save_states=True)
+    assert maxabs(got["states"], ref["states"]) <= 1e-10
+    assert maxabs(got["expect"], ref["expect"]) <= 1e-10
+
+
+def test_grid_non_hermitian_h_full_mode():
+    """H with an anti-Hermitian part keeps rho from staying Hermitian; the
+    kernel detects it and integrates every entry."""
+    s = W.jaynes_cummings(N=10)
+    n = s.H.shape[0]
+    Hn = np.asarray(s.H.todense() if hasattr(s.H, "todense") else s.H, dtype=complex)
+    Hn = Hn - 0.05j * np.diag(np.arange(n) / n)
+    tl = np.linspace(0, 1.0, 3)
+    ref = oracle_mesolve(Hn, s.c_ops, s.e_ops, s.psi0, tl, fixed_dt=0.02, save_states=True,
+                         rhs="product")
+    qtl = require_gpu()
+    g = qtl.System(Hn, s.c_ops, s.e_ops)
+    try:
+        got = g.mesolve(s.psi0, tl, fixed_dt=0.02, save_states=True, engine="grid")
+    finally:
+        g.free()
+    assert maxabs(got["states"], ref["states"]) <= 1e-10
+
+
+def test_grid_hermitian_mode_matches_full_mode():
+    """The same Hermitian problem with and without a rounding-size
+    anti-Hermitian part in rho0 (above the 1e-13 threshold: full mode) gives
+    the same trajectory to well within the parity tolerance."""
+    s = W.ising_chain(6, h=0.8)
+    n = s.H.shape[0]
+    psi = np.asarray(s.psi0)
+    rho0 = np.outer(psi, psi.conj())
+    rng = np.random.default_rng(5)
+    pert = 1e-11 * (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    tl = np.linspace(0, 0.5, 3)
+    a = _gpu_state(s, rho0, tl, fixed_dt=0.01, save_states=True)
+    b = _gpu_state(s, rho0 + pert, tl, fixed_dt=0.01, save_states=True)
+    ref = oracle_mesolve(s.H, s.c_ops, s.e_ops, rho0, tl, fixed_dt=0.01, save_states=True,
+                         rhs="product")
+    assert maxabs(a["states"], ref["states"]) <= 1e-10
+    assert maxabs(b["states"], ref["states"]) <= 1e-9
