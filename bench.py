@@ -384,9 +384,25 @@ def run_sweep(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     hs = [h.handle for h in handles]
 
+    # one-shot batched calls (host planning and launches every call), for context
+    direct = []
+    for _ in range(2):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        qtl.mesolve_batch_async(hs, states, [1] * len(hs), tl, opts, exps, info)
+        e1.record(main)
+        torch.cuda.synchronize(dev)
+        direct.append(e0.elapsed_time(e1))
+    # the plan: cluster size per group autotuned, launch sequence captured in a
+    # CUDA graph; every timed step replays it
+    t_plan = time.perf_counter()
+    plan = qtl.Batch(hs, states, [1] * len(hs), tl, opts, exps, info, autotune=True)
+    t_plan = time.perf_counter() - t_plan
+
     def step():
-        keep = qtl.mesolve_batch_async(hs, states, [1] * len(hs), tl, opts, exps, info)
-        return keep
+        plan.launch(main.cuda_stream)
     for _ in range(args.warmup):
         step()
         torch.cuda.synchronize(dev)
@@ -399,12 +415,13 @@ def run_sweep(args):
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(main)
-        keep = step()
+        step()
         e1.record(main)
         torch.cuda.synchronize(dev)
         ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
     inf = info.cpu().numpy()
+    groups = plan.groups()
     rhs = int(inf[:, 3].sum())
     bad = int(((inf[:, 0] & 0xffffffff) != 0).sum())
     mean_ms = statistics.mean(ms)
@@ -416,9 +433,13 @@ def run_sweep(args):
            "config": {"workload": "kerr_sweep_1024: N~U{10..60}, t in [0,50], 101 saveat, mixed, rtol 1e-7 atol 1e-9",
                       "l2": "flushed (512 MB write) between timed steps"},
            "solves_per_s": world * len(hs) / (mean_ms / 1e3), "failed_solves": bad,
+           "plan": {"graph_replay": True, "build_s": t_plan, "direct_call_ms": statistics.mean(direct),
+                    "groups": [{"cluster": c, "solves": n, "probe_ms": {str(cc): round(t, 3) for cc, t in cand}}
+                               for c, n, cand in groups]},
            "rhs_evals_per_step": rhs, "gpu_launches": qtl.launch_count() - launches0, "clocks": clk}
     if rank == 0:
         print(json.dumps(out))
+    plan.free()
     for h in handles:
         h.free()
 

@@ -210,6 +210,46 @@ qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb, const qtl_c
                              const int32_t* is_ket, const double* tlist, int32_t nt,
                              const qtl_opts* opts, qtl_c128* const* expect_out, qtl_stats* stats);
 
+/* Reusable batch plan (Sec. 3.2 over nb independent systems, as
+ * qtl_mesolve_batch_async), built once and replayed.
+ *   qtl_batch_create: the same arguments as qtl_mesolve_batch_async (device
+ *     pointers, which the plan keeps: each launch reads state0_dev[b] and
+ *     tlist_dev and writes expect_dev[b] and info_dev[b] as they are then)
+ *     plus autotune.  Systems are grouped by the launch plan their size
+ *     implies.  autotune = 1: for every group with more than one feasible
+ *     cluster size among C/2, C, 2C, 4C, each candidate integrates the
+ *     group's own solves over the first 5% of tlist's span (two output times,
+ *     outputs into the plan's scratch) once to warm up and once timed with
+ *     CUDA events on opts->cuda_stream, and the fastest is kept.  The job
+ *     table is built on the device, and the launch sequence (status reset,
+ *     one cluster launch per group on a stream of the plan's own, the join)
+ *     is captured once in a CUDA graph.  Blocks until the plan is ready.
+ *     The systems and device buffers must outlive the plan.  Returns
+ *     QTL_ETOOBIG if a group does not fit the cluster kernel, QTL_ENOMEM if
+ *     the plan's scratch cannot be allocated, QTL_ECUDA on a CUDA error.
+ *   qtl_batch_launch: replays the graph on cuda_stream (a cudaStream_t of the
+ *     device the plan was created on; else QTL_EINVAL).  Launches on one plan
+ *     share its scratch, so they must not overlap: enqueue them on one
+ *     stream.  A solve's result equals qtl_mesolve with opts->cluster_size =
+ *     its group's cluster size.
+ *   qtl_batch_groups / qtl_batch_group_info: number of groups; for group k
+ *     its cluster size, number of solves, and the autotuner's candidates
+ *     (ncand, cand_cluster[ncand], cand_ms[ncand]: probe time in ms; ncand =
+ *     0 when not tuned).  Output pointers may be NULL.
+ *   qtl_batch_group_of: the group of system index sys (-1 if out of range).
+ *   qtl_batch_free: releases the plan (NULL is a no-op). */
+typedef struct qtl_batch qtl_batch;
+qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb, const qtl_c128* const* state0_dev,
+                            const int32_t* is_ket, const double* tlist_dev, int32_t nt, const qtl_opts* opts,
+                            qtl_c128* const* expect_dev, qtl_device_info* info_dev, int32_t autotune,
+                            qtl_batch** out);
+qtl_status qtl_batch_launch(qtl_batch* b, void* cuda_stream);
+int32_t qtl_batch_groups(const qtl_batch* b);
+qtl_status qtl_batch_group_info(const qtl_batch* b, int32_t k, int32_t* cluster_size, int32_t* nsolves,
+                                int32_t* ncand, int32_t* cand_cluster, double* cand_ms);
+int32_t qtl_batch_group_of(const qtl_batch* b, int32_t sys);
+void qtl_batch_free(qtl_batch* b);
+
 /* mcsolve (Sec. 3.3): ntraj trajectories from the ket psi0[n].
  *   seed      64-bit key of the per-trajectory Philox4x32-10 streams: draw d
  *             of trajectory j uses counter (d, traj_offset + j, 0, 0) and key

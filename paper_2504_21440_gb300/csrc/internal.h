@@ -265,6 +265,14 @@ cudaError_t mc_wide_plan(const McJob& job, int precision, McWidePlan* plan);
 cudaError_t launch_mc_wide(const McJob& job, int precision, const McWidePlan& plan, void* scratch,
                            const SellConst* cdesc, cudaStream_t st);
 
+// host helpers shared by the solve entry points (runtime.cpp)
+qtl_status ensure_liouvillian(System& s);
+void batch_plan(int L, int* C, int* rpt);
+int64_t cta_nnz_max(const System& s, int C);
+void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, const qtl_c128* state0_dev,
+                 int is_ket, double* epart, qtl_c128* expect_dev, qtl_device_info* info_dev,
+                 const qtl_opts* opts, int smem_nnz);
+
 void count_launch(int k = 1);
 void set_cuda_error(cudaError_t e);
 

@@ -554,7 +554,7 @@ static qtl_status ensure_grid(System& s) {
     return QTL_OK;
 }
 
-static qtl_status ensure_liouvillian(System& s) {
+qtl_status ensure_liouvillian(System& s) {
     std::lock_guard<std::mutex> lk(g_build_mu);
     if (s.dL.rp) return QTL_OK;
     if ((int64_t)s.n * s.n > me_cluster_capacity()) return QTL_ETOOBIG;
@@ -711,6 +711,53 @@ qtl_status mesolve_grid(System& s, const qtl_c128* state0_dev, int32_t is_ket, c
         return QTL_ECUDA;
     }
     return QTL_OK;
+}
+
+
+// Launch plan of one system in a batch: cluster size from its own size.
+void batch_plan(int L, int* C, int* rpt) {
+    int c = 1;
+    while (c < 16 && (int64_t)c * 1024 < L) c *= 2;
+    me_plan(L, c, C, rpt);
+}
+
+int64_t cta_nnz_max(const System& s, int C) {
+    const int L = s.n * s.n;
+    std::vector<int64_t> per(C, 0);
+    for (int r = 0; r < L; ++r) per[r % C] += s.L_rp[r + 1] - s.L_rp[r];
+    return *std::max_element(per.begin(), per.end());
+}
+
+// One cluster-kernel job: system s from state0 over tlist with opts.
+void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, const qtl_c128* state0_dev,
+                 int is_ket, double* epart, qtl_c128* expect_dev, qtl_device_info* info_dev,
+                 const qtl_opts* opts, int smem_nnz) {
+    std::memset(&J, 0, sizeof(J));
+    J.n = s.n;
+    J.L = s.n * s.n;
+    J.seg = s.dL.seg;
+    J.ci = s.dL.ci;
+    J.lv64 = s.dL.v64;
+    J.lv32 = s.dL.v32;
+    J.n_e = s.n_e;
+    J.ew = s.ew;
+    J.tlist = tlist_dev;
+    J.nt = nt;
+    J.state0 = (const double2*)state0_dev;
+    J.is_ket = is_ket ? 1 : 0;
+    J.epart = epart;
+    J.expect = (double2*)expect_dev;
+    J.states = nullptr;
+    J.info = info_dev;
+    J.rtol = opts->rtol;
+    J.atol = opts->atol;
+    J.dt0 = opts->dt0;
+    J.dt_min = opts->dt_min;
+    J.dt_fixed = opts->dt_fixed;
+    J.max_steps = opts->max_steps;
+    J.fixed = opts->fixed_step ? 1 : 0;
+    J.method = opts->method;
+    J.smem_nnz = smem_nnz;
 }
 
 }  // namespace qtl
@@ -952,21 +999,8 @@ qtl_status fork_streams(int k, cudaStream_t** out) {
     return QTL_OK;
 }
 
-// Launch plan of one system in a batch: cluster size from its own size.
-void batch_plan(int L, int* C, int* rpt) {
-    int c = 1;
-    while (c < 16 && (int64_t)c * 1024 < L) c *= 2;
-    me_plan(L, c, C, rpt);
-}
-
-int64_t cta_nnz_max(const System& s, int C) {
-    const int L = s.n * s.n;
-    std::vector<int64_t> per(C, 0);
-    for (int r = 0; r < L; ++r) per[r % C] += s.L_rp[r + 1] - s.L_rp[r];
-    return *std::max_element(per.begin(), per.end());
-}
-
 }  // namespace
+
 
 extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_t nb,
                                               const qtl_c128* const* state0_dev, const int32_t* is_ket,
@@ -1023,36 +1057,9 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
     int q = 0;
     for (int k = 0; k < nk; ++k) {
         first[k] = q;
-        for (int b : bucket[k]) {
-            System& s = systems[b]->s;
-            MeJob& J = jobs[q++];
-            std::memset(&J, 0, sizeof(J));
-            J.n = s.n;
-            J.L = s.n * s.n;
-            J.seg = s.dL.seg;
-            J.ci = s.dL.ci;
-            J.lv64 = s.dL.v64;
-            J.lv32 = s.dL.v32;
-            J.n_e = s.n_e;
-            J.ew = s.ew;
-            J.tlist = tlist_dev;
-            J.nt = nt;
-            J.state0 = (const double2*)state0_dev[b];
-            J.is_ket = is_ket[b] ? 1 : 0;
-            J.epart = (double*)(scratch + ep_off[b]);
-            J.expect = (double2*)expect_dev[b];
-            J.states = nullptr;
-            J.info = info_dev + b;
-            J.rtol = opts->rtol;
-            J.atol = opts->atol;
-            J.dt0 = opts->dt0;
-            J.dt_min = opts->dt_min;
-            J.dt_fixed = opts->dt_fixed;
-            J.max_steps = opts->max_steps;
-            J.fixed = opts->fixed_step ? 1 : 0;
-            J.method = opts->method;
-            J.smem_nnz = 0;
-        }
+        for (int b : bucket[k])
+            me_job_fill(jobs[q++], systems[b]->s, tlist_dev, nt, state0_dev[b], is_ket[b],
+                        (double*)(scratch + ep_off[b]), expect_dev[b], info_dev + b, opts, 0);
     }
     first[nk] = q;
     for (int k = 0; k < nk; ++k) {

@@ -106,6 +106,19 @@ def load():
     lib.qtl_mesolve_batch.restype = C.c_int
     lib.qtl_mesolve_batch_async.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P]
     lib.qtl_mesolve_batch_async.restype = C.c_int
+    lib.qtl_batch_create.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P, C.c_int32,
+                                     C.POINTER(P)]
+    lib.qtl_batch_create.restype = C.c_int
+    lib.qtl_batch_launch.argtypes = [P, P]
+    lib.qtl_batch_launch.restype = C.c_int
+    lib.qtl_batch_groups.argtypes = [P]
+    lib.qtl_batch_groups.restype = C.c_int32
+    lib.qtl_batch_group_info.argtypes = [P, C.c_int32, P, P, P, P, P]
+    lib.qtl_batch_group_info.restype = C.c_int
+    lib.qtl_batch_group_of.argtypes = [P, C.c_int32]
+    lib.qtl_batch_group_of.restype = C.c_int32
+    lib.qtl_batch_free.argtypes = [P]
+    lib.qtl_batch_free.restype = None
     lib.qtl_mcsolve_noalloc.argtypes = [C.c_int32, P, P, P, C.c_int64, C.c_int32, P, P, P,
                                         C.c_int32, P, P, P, P, P, C.c_int32, C.c_int32,
                                         C.c_uint64, C.c_int64, C.POINTER(Opts), P, P]
@@ -321,6 +334,53 @@ def mesolve_batch_async(handles, states_dev, is_ket, tlist_dev, opts, expects_de
     _check(load().qtl_mesolve_batch_async(harr, nb, sarr, karr, _ptr(tlist_dev), int(tlist_dev.numel()),
                                           C.byref(opts), earr, _ptr(info_dev)), "qtl_mesolve_batch_async")
     return (harr, sarr, karr, earr)
+
+
+class Batch:
+    """qtl_batch_*: a batch plan over device tensors (kept alive here),
+    optionally autotuned, replayed from a captured CUDA graph by launch()."""
+
+    def __init__(self, handles, states_dev, is_ket, tlist_dev, opts, expects_dev, info_dev, autotune=False):
+        nb = len(handles)
+        self._keep = (list(states_dev), tlist_dev, list(expects_dev), info_dev)
+        harr = (C.c_void_p * nb)(*[h.value if hasattr(h, "value") else h for h in handles])
+        sarr = (C.c_void_p * nb)(*[x.data_ptr() for x in states_dev])
+        karr = (C.c_int32 * nb)(*[int(k) for k in is_ket])
+        earr = (C.c_void_p * nb)(*[x.data_ptr() for x in expects_dev])
+        self.handle = C.c_void_p()
+        _check(load().qtl_batch_create(harr, nb, sarr, karr, _ptr(tlist_dev), int(tlist_dev.numel()),
+                                       C.byref(opts), earr, _ptr(info_dev), 1 if autotune else 0,
+                                       C.byref(self.handle)), "qtl_batch_create")
+
+    def launch(self, stream):
+        _check(load().qtl_batch_launch(self.handle, C.c_void_p(int(stream))), "qtl_batch_launch")
+
+    def groups(self):
+        """[(cluster_size, nsolves, [(candidate cluster size, probe ms), ...]), ...]"""
+        lib = load()
+        out = []
+        for k in range(int(lib.qtl_batch_groups(self.handle))):
+            cs, ns, nc = C.c_int32(), C.c_int32(), C.c_int32()
+            cc = (C.c_int32 * 8)()
+            cm = (C.c_double * 8)()
+            _check(lib.qtl_batch_group_info(self.handle, k, C.byref(cs), C.byref(ns), C.byref(nc), cc, cm),
+                   "qtl_batch_group_info")
+            out.append((cs.value, ns.value, [(cc[i], cm[i]) for i in range(nc.value)]))
+        return out
+
+    def group_of(self, b):
+        return int(load().qtl_batch_group_of(self.handle, int(b)))
+
+    def free(self):
+        if self.handle:
+            load().qtl_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class Server:
