@@ -635,7 +635,48 @@ def run_serving(args):
                               "mcsolve": sum(r["kind"] == "mcsolve" for r in reqs)}})
     print(json.dumps({"metric": "p50/p99 solve latency and solves/s under Poisson arrivals",
                       "workload": "serving mix: coupled-cavity mesolve (n 16-1024) + Ising mcsolve (8-14 spins)",
-                      "dtype": "f32 RHS / f64 state", "data": "synthetic", "n_gpus": 1, "rates": lines}))
+                      "dtype": "f32 RHS / f64 state", "data": "synthetic", "n_gpus": 1, "rates": lines,
+                      "vs_fp64_single_solve": serving_vs_fp64(qtl, opts)}))
+
+
+def serving_vs_fp64(qtl, opts_mixed, n_req=40):
+    """The same bounded request sample (the first n_req requests of the mix
+    with 8-10-spin chains, all arrived at once) through the server in mixed
+    precision and through the plain FP64 single-solve path, one request after
+    the other.  Reports solves/s of both and, for the mesolve requests, the
+    largest difference of an expectation value between the two (mcsolve
+    means differ by the statistics of trajectories whose jump times move with
+    the precision, so they are not compared value by value)."""
+    reqs = W.serving_mix(n_requests=n_req, seed=5, rate=1e6, ising_spins=(8, 10))
+    systems = [qtl.System(r["system"].H, r["system"].c_ops, r["system"].e_ops) for r in reqs]
+    o64 = qtl.make_opts(precision="fp64", rtol=1e-7, atol=1e-9)
+    srv = qtl.Server(max_inflight=8)
+    r0, g0 = reqs[0], systems[0]   # warm-up
+    srv.wait(srv.submit(r0["kind"], g0, r0["system"].psi0, r0["system"].tlist, opts_mixed,
+                        ntraj=r0.get("ntraj", 0), seed=r0.get("seed", 0)))
+    t0 = time.perf_counter()
+    tickets = [srv.submit(r["kind"], g, r["system"].psi0, r["system"].tlist, opts_mixed,
+                          ntraj=r.get("ntraj", 0), seed=r.get("seed", 0)) for r, g in zip(reqs, systems)]
+    served = [srv.wait(t) for t in tickets]
+    t_srv = time.perf_counter() - t0
+    srv.free()
+    t0 = time.perf_counter()
+    single = []
+    for r, g in zip(reqs, systems):
+        sy = r["system"]
+        if r["kind"] == "mesolve":
+            single.append(qtl.mesolve(g.handle, g.n_e, sy.psi0, sy.tlist, o64))
+        else:
+            single.append(qtl.mcsolve(g.handle, g.n_e, sy.psi0, sy.tlist, r["ntraj"], r["seed"], o64))
+    t_one = time.perf_counter() - t0
+    for g in systems:
+        g.free()
+    me = [float(np.max(np.abs(np.asarray(a["expect"]) - b["expect"])))
+          for a, b, r in zip(served, single, reqs) if r["kind"] == "mesolve"]
+    return {"requests": n_req, "sample": "first %d requests of the mix, 8-10-spin chains, all arrived at t=0" % n_req,
+            "served_mixed_solves_per_s": n_req / t_srv, "fp64_single_solves_per_s": n_req / t_one,
+            "speedup": t_one / t_srv, "mesolve_max_abs_diff_vs_fp64": max(me) if me else None,
+            "failed": sum(1 for r in served if r["status"] != 0)}
 
 
 def main():
