@@ -17,6 +17,8 @@ step after the paper:
   mesolve.py   mesolve with expectation values Tr(O rho) (Sec. 3.2)
   philox.py    Philox4x32-10 counter-based generator (Salmon et al. 2011)
   mcsolve.py   Monte-Carlo wave-function method (Sec. 3.3)
+  timedep.py   time-dependent Hamiltonians H0 + sum_k f_k(t) H_k (Sec. 2,
+               Sec. 3.2) for mesolve and mcsolve; sesolve (Sec. 3.1)
 
 Parity status: every function here is pinned by tests/test_oracle_*.py to
 closed forms, brute-force matrix exponentials, invariants, order conditions

@@ -17,6 +17,8 @@ Readings where the paper is silent (shared with the CUDA library):
     the bracket is narrower than 1e-10 max(1, |t|) or after 30 evaluations;
     the jump is taken at the last evaluated point;
   * the channel is the smallest k with sum_{j<=k} p_j >= u sum_j p_j;
+  * with no collapse operator the threshold is 0, so a trajectory never
+    jumps (the Schroedinger equation);
   * draws per trajectory alternate: threshold, channel, threshold, ...
   * expectation values <psi|O|psi>/<psi|psi> are recorded at each tlist time
     and averaged arithmetically over trajectories.
@@ -51,10 +53,16 @@ def trajectory(Heff, c_ops, e_ops, psi0, tlist, seed, traj_id, method="tsit5",
         draws[0] += 1
         return u
 
-    def f(t, psi):
-        return -1j * (Heff @ psi)
+    if callable(Heff):       # time-dependent H_eff(t) applied to psi
+        def f(t, psi):
+            return -1j * Heff(t, psi)
+    else:
+        def f(t, psi):
+            return -1j * (Heff @ psi)
 
-    r = [draw()]
+    # without collapse operators there is no channel to jump to: the norm is
+    # compared with a threshold of 0 (the first draw is still consumed)
+    r = [draw() if len(c_ops) > 0 else (draw(), 0.0)[1]]
     jump_times, jump_channels = [], []
     n_e = len(e_ops)
     expect = np.zeros((n_e, len(tlist)), dtype=np.complex128)
