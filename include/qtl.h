@@ -150,6 +150,33 @@ void qtl_opts_default(qtl_opts* opts);
 qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c,
                              const qtl_op* e_ops, int32_t n_e, qtl_system** out);
 
+/* Time-dependent Hamiltonians (Sec. 2, QobjEvo: H(t) = H0 + sum_k f_k(t) H_k;
+ * the drive F cos(w_d t)(a + a^dag) of Sec. 3.2; the complex pair
+ * A e^{i w t} a + conj(.) a^dag of Sec. 5).  A coefficient is
+ *   f(t) = (amp_re + i amp_im) * env(t) * g(omega t + phi),
+ *   g = cos for QTL_COEF_COS, exp(i .) for QTL_COEF_EXP,
+ *   env(t) = exp(-(t - t0)^2 / (2 sigma^2)) if sigma > 0, else 1,
+ * evaluated in FP64 at every stage time of the integrator. */
+typedef enum { QTL_COEF_COS = 0, QTL_COEF_EXP = 1 } qtl_coef_kind;
+typedef struct {
+    int32_t kind;
+    double amp_re, amp_im, omega, phi, t0, sigma;
+} qtl_coef;
+
+/* Adds the term f(t) Hk to the system's Hamiltonian (H of qtl_system_create
+ * becomes H0).  Up to 8 terms; Hk has the system's dimension n <= 1024.
+ * Terms must be added before the system's first solve (QTL_EINVAL after).
+ * Which solvers take them: qtl_sesolve and qtl_mcsolve (trajectories with
+ * n <= 1024, FP64 or mixed precision: A(t) = A - i sum_k f_k(t) H_k), and
+ * qtl_mesolve / qtl_mesolve_async in FP64 on the grid kernel (the automatic
+ * engine picks it; the cluster engine, mixed precision, batches and plans
+ * return QTL_EINVAL for such a system).  The grid kernel integrates only the
+ * lower triangle of rho when H0 and every H_k are exactly Hermitian and
+ * every f_k is real (QTL_COEF_COS with amp_im = 0).
+ * Errors: QTL_EINVAL (NULL, bad operator or coefficient, 8 terms already,
+ * n > 1024, a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
+qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f);
+
 /* Releases the system and its device memory (NULL is a no-op).  Work enqueued
  * by _async calls on the system must have completed. */
 void qtl_system_free(qtl_system* sys);
@@ -209,6 +236,14 @@ qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_t nb,
 qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb, const qtl_c128* const* state0,
                              const int32_t* is_ket, const double* tlist, int32_t nt,
                              const qtl_opts* opts, qtl_c128* const* expect_out, qtl_stats* stats);
+
+/* sesolve (Sec. 3.1): d psi/dt = -i H(t) psi from psi0[n] for a system
+ * without collapse operators (QTL_EINVAL otherwise), n <= 1024: the
+ * trajectory kernel with one trajectory, which never jumps.
+ *   expect_out[n_e*nt]: <psi|O_k|psi>/<psi|psi> at each time of tlist.
+ * Host pointers; returns when done; opts as for qtl_mcsolve. */
+qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                       const qtl_opts* opts, qtl_c128* expect_out, qtl_stats* stats);
 
 /* Reusable batch plan (Sec. 3.2 over nb independent systems, as
  * qtl_mesolve_batch_async), built once and replayed.

@@ -96,6 +96,8 @@ extern "C" qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb,
     if (st != QTL_OK) return st;
     for (int b = 0; b < nb; ++b) {
         if (!systems[b] || !state0_dev[b] || (systems[b]->s.n_e > 0 && !expect_dev[b])) return QTL_EINVAL;
+        if (!systems[b]->s.Htd.empty()) return QTL_EINVAL;   // time-dependent H: not on the cluster kernel
+        systems[b]->s.solved = true;
         if ((st = ensure_liouvillian(systems[b]->s)) != QTL_OK) return st;
     }
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;

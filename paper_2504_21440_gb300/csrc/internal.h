@@ -80,6 +80,17 @@ struct SellConst {
     int4 d[SELL_CDESC];
 };
 
+// One operator in pattern-compressed sliced ELLPACK, as the kernels read it.
+struct SellRef {
+    const int4* sl;       // [2 nslices]
+    const int4* desc;
+    const int32_t* ci;
+    const double* vs64;
+    const float* vs32;
+    const double2* vc64;
+    const float2* vc32;
+};
+
 // ---------------------------------------------------------------- system
 struct System {
     int n = 0, n_c = 0, n_e = 0;
@@ -98,8 +109,16 @@ struct System {
     DevSell sBt;          // B^T in sliced ELLPACK (built lazily: grid mesolve)
     int2* units = nullptr;      // grid-mesolve work units (built with sBt)
     int nu_tri = 0, nu_all = 0;
-    int herm_h = 0;             // H == H^dag exactly
+    int herm_h = 0;             // H == H^dag exactly (and every time-dependent term real and Hermitian)
     int c_real = 0;             // every collapse-operator value is real
+    std::vector<Csr> Htd;       // time-dependent terms f_k(t) H_k
+    std::vector<qtl_coef> ftd;
+    DevCsr dT;                  // -i H_k stacked row-wise, segmented (trajectory kernel)
+    std::vector<DevSell> sTa;   // -i H_k in sliced ELLPACK (grid kernel)
+    std::vector<DevSell> sTb;   // (i H_k)^T in sliced ELLPACK (grid kernel)
+    qtl_coef* d_tf = nullptr;   // device copy of ftd
+    SellRef* d_tsl = nullptr;   // device [2 n_td] references to sTa, sTb (grid kernel)
+    bool solved = false;        // a solve has run: no more terms
     std::vector<int32_t> L_rp;  // host copy of its row pointers (shared-memory sizing)
     double2* ew = nullptr;      // [n*n][n_e] trace weights (built with the Liouvillian)
     int32_t* cmap = nullptr;    // [n_c][n] column of C_c's entry in row i, -1 if none
@@ -132,16 +151,9 @@ struct MeJob {
     int smem_nnz;         // per-CTA shared-memory capacity for Liouvillian entries
 };
 
-// One operator in pattern-compressed sliced ELLPACK, as the kernels read it.
-struct SellRef {
-    const int4* sl;       // [2 nslices]
-    const int4* desc;
-    const int32_t* ci;
-    const double* vs64;
-    const float* vs32;
-    const double2* vc64;
-    const float2* vc32;
-};
+// Time-dependent Hamiltonian terms f_k(t) H_k per system (qtl_system_add_td).
+constexpr int QTL_MAX_TD = 8;
+
 
 // Large-rho mesolve (one cooperative grid per solve, product-form RHS).
 struct MgJob {
@@ -152,8 +164,11 @@ struct MgJob {
     const int2* units;    // warp work units {row slice, column group}; the
                           // units meeting the lower triangle come first
     int nu_tri, nu_all;
-    int herm_h;           // H is exactly Hermitian
+    int herm_h;           // H(t) is exactly Hermitian at every t
     int c_real;           // every collapse-operator value is real (cmap path)
+    int n_td;             // time-dependent terms (FP64 kernel only)
+    const SellRef* tsl;   // device [2 n_td]: -i H_k for k < n_td, then (i H_k)^T
+    const qtl_coef* tf;   // device [n_td] coefficients
     int n_c;
     const int32_t* crp;   // collapse operators stacked row-wise (plain CSR)
     const int32_t* cci;
@@ -206,6 +221,12 @@ struct McJob {
     const int32_t* oci;
     const double2* ov;
     const int4* oseg;     // their row segments (real-only | imaginary-only | complex), or null
+    int n_td;             // time-dependent terms f_k(t) (-i H_k), trajectory kernel n <= 1024
+    const int4* tseg;     // -i H_k stacked row-wise (rows k*n + r), segmented
+    const int32_t* tci;
+    const double2* tv64;
+    const float2* tv32;
+    const qtl_coef* tf;   // device [n_td] coefficients
     const double* tlist;
     int nt;
     const double2* psi0;

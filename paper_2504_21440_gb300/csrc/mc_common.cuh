@@ -3,6 +3,7 @@
 #pragma once
 #include "internal.h"
 #include "rk.cuh"
+#include "td.cuh"
 
 namespace qtl {
 
@@ -181,6 +182,11 @@ struct McCtl {
     int action, land, accept, save, rsave, ch, rootgo, pub;
     float wf[MC_MAXWARPS];
     double wd[MC_MAXWARPS];
+    // time-dependent terms: f_k at the stage times t + c_s htry (slots 1..6)
+    // and at one other time (slot 7); tnow = the step's start
+    double tnow;
+    double2 tdf[8][QTL_MAX_TD];
+    float2 tdf32[8][QTL_MAX_TD];
 };
 
 // index of h*a_sj in McCtl::coef (stages packed row by row)

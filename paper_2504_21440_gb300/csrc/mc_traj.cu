@@ -58,9 +58,31 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
         }
         __syncthreads();
     }
-    auto rhs_row = [&](int r, const T2* x) -> T2 {
-        return cached ? mc_spmv_row_s<T2, TV>(r, s_seg, s_ci, s_v, x)
+    // A x, plus sum_k f_k(t) (-i H_k) x with the coefficients of slot `slot`
+    // (1..6: the stages of the current step, 7: one other time)
+    const TV* tv = MIXED ? (const TV*)J.tv32 : (const TV*)J.tv64;
+    auto rhs_row = [&](int r, const T2* x, int slot) -> T2 {
+        T2 v = cached ? mc_spmv_row_s<T2, TV>(r, s_seg, s_ci, s_v, x)
                       : mc_spmv_row<T2, TV>(r, J.aseg, J.aci, av, x);
+        for (int k = 0; k < J.n_td; ++k) {
+            const T2 w = mc_spmv_row<T2, TV>(k * n + r, J.tseg, J.tci, tv, x);
+            T2 f;
+            if constexpr (MIXED)
+                f = cb.tdf32[slot][k];
+            else
+                f = cb.tdf[slot][k];
+            v.x += f.x * w.x - f.y * w.y;
+            v.y += f.x * w.y + f.y * w.x;
+        }
+        return v;
+    };
+    // warp 0: f_k at time tp into slot 7
+    auto publish_td_at = [&](double tp) {
+        if (lane < J.n_td) {
+            const double2 f = td_coef(J.tf[lane], tp);
+            cb.tdf[7][lane] = f;
+            cb.tdf32[7][lane] = make_float2((float)f.x, (float)f.y);
+        }
     };
 
     long long acc_steps = 0, rej_steps = 0, rhs_evals = 0, jumps = 0;  // thread 0
@@ -98,10 +120,11 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
             }
         }
         sync_yf();
+        if (warp == 0 && J.n_td > 0) publish_td_at(J.tlist[0]);
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < RPT; ++m)
-            if (own[m]) k[0][m] = rhs_row(row[m], ys0);
+            if (own[m]) k[0][m] = rhs_row(row[m], ys0, 7);
 
         // <psi|O_e|psi>/<psi|psi> from the FP64 copy in yd (all rows written and
         // synchronised by the caller); returns |psi|^2 in thread 0.
@@ -150,6 +173,7 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
         ctl.init();
         if (tid == 0) {
             r = philox_uniform(J.seed, traj, draw++);
+            if (J.n_c == 0) r = 0.0;   // no channel to jump to: never below the threshold
             rhs_evals += 1;
         }
         // ---- starting step ----
@@ -180,12 +204,13 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                 const double2 f0 = to_d2_mc(k[0][m]);
                 ys1[row[m]] = from_d2_mc<T2>(make_double2(y[m].x + h0 * f0.x, y[m].y + h0 * f0.y));
             }
+            if (warp == 0 && J.n_td > 0) publish_td_at(J.tlist[0] + h0);
             __syncthreads();
             double s2 = 0.0;
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
                 if (!own[m]) continue;
-                const double2 f1 = to_d2_mc(rhs_row(row[m], ys1));
+                const double2 f1 = to_d2_mc(rhs_row(row[m], ys1, 7));
                 const double2 f0 = to_d2_mc(k[0][m]);
                 const float sc = (float)J.atol + (float)J.rtol * sqrtf((float)(y[m].x * y[m].x + y[m].y * y[m].y));
                 const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
@@ -202,6 +227,7 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
 
         auto next_action = [&]() {
             cb.pub = 0;
+            cb.tnow = t;
             for (;;) {
                 if (status != QTL_OK || idx >= J.nt) {
                     cb.action = MC_DONE;
@@ -253,6 +279,13 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                     cb.coef[lane] = c;
                     cb.coeff[lane] = (float)c;
                 }
+                // f_k at the stage times t + c_s htry (slots 1..6)
+                for (int i = lane; i < 6 * J.n_td; i += 32) {
+                    const int s = 1 + i / J.n_td, kk = i % J.n_td;
+                    const double2 f = td_coef(J.tf[kk], cb.tnow + tab.c[s] * hh);
+                    cb.tdf[s][kk] = f;
+                    cb.tdf32[s][kk] = make_float2((float)f.x, (float)f.y);
+                }
             }
             __syncwarp();
         };
@@ -296,7 +329,7 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                 __syncthreads();
 #pragma unroll
                 for (int m = 0; m < RPT; ++m)
-                    if (own[m]) k[s][m] = rhs_row(row[m], ysb);
+                    if (own[m]) k[s][m] = rhs_row(row[m], ysb, s);
             }
         };
         // |ynew|^2 (FP64) and the FP32 error sum, warp -> thread 0.
@@ -562,10 +595,11 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                 }
             }
             sync_yf();
+            if (warp == 0 && J.n_td > 0) publish_td_at(cb.tnow);
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < RPT; ++m)
-                if (own[m]) k[0][m] = rhs_row(row[m], ys0);
+                if (own[m]) k[0][m] = rhs_row(row[m], ys0, 7);
             double n2 = 0.0;
             norm2_ynew(&n2);  // ynew == y here: |psi|^2 after the jump
             if (tid == 0) norm2 = n2;

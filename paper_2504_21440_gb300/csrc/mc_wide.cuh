@@ -408,6 +408,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             attempts = 0;
             ctl.init();
             r = philox_uniform(J.seed, traj, draw++);
+            if (J.n_c == 0) r = 0.0;   // no channel to jump to: never below the threshold
             rhs_evals += 1;
         }
         // ---- starting step ----

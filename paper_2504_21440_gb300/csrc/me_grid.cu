@@ -41,6 +41,7 @@
 
 #include "internal.h"
 #include "rk.cuh"
+#include "td.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -81,6 +82,8 @@ struct MgShared {
     double h0, d1;
     float red_a, red_b;
     int action, land, accept, save_idx, repeat_idx, refresh_now;
+    double tnow;                     // the step's start (time-dependent terms)
+    double2 tdf[7][QTL_MAX_TD];      // f_k at t + c_s h (slots 1..6) and at one other time (slot 0)
 };
 
 __device__ __forceinline__ double2 g_to_d2(double2 v) { return v; }
@@ -255,9 +258,10 @@ __device__ __forceinline__ void mg_b_group(const SellRef& B, const MgVals<MIXED>
 
 // The product-form right-hand side A Y + Y B + sum_c C_c Y C_c^dag on one
 // unit; out[k] is entry (a, b0 + k) (garbage where a or b0 + k >= n).
-template <bool MIXED, int CB>
+template <bool MIXED, int CB, bool TD = !MIXED>
 __device__ __forceinline__ void rhs_unit(const MgJob& J, const typename GPrec<MIXED>::T2* __restrict__ Y,
-                                         int s, int b0, int lane, typename GPrec<MIXED>::T2 (&out)[CB]) {
+                                         int s, int b0, int lane, typename GPrec<MIXED>::T2 (&out)[CB],
+                                         const double2* __restrict__ tdf = nullptr) {
     using T = typename GPrec<MIXED>::T;
     using T2 = typename GPrec<MIXED>::T2;
     const int nn = J.n;
@@ -290,6 +294,41 @@ __device__ __forceinline__ void rhs_unit(const MgJob& J, const typename GPrec<MI
         mg_b_group<0, CB, MIXED, T, T2>(J.bt, V, h0.x, h0.y, h1.x, h1.y, Y, n, nn, a, arow, b0, yo, ar, ai);
         mg_b_group<1, CB, MIXED, T, T2>(J.bt, V, h0.x + h0.y, h0.z, h1.x, h1.y, Y, n, nn, a, arow, b0, yo, ar, ai);
         mg_b_group<2, CB, MIXED, T, T2>(J.bt, V, h0.x + h0.y + h0.z, h0.w, h1.x, h1.z, Y, n, nn, a, arow, b0, yo, ar, ai);
+    }
+    // time-dependent terms (FP64 solves): f_k(t) ((-i H_k) Y + Y (i H_k))
+    if constexpr (TD) {
+        for (int q = 0; q < J.n_td; ++q) {
+            T tr[CB], ti[CB];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) tr[k] = ti[k] = 0;
+            {
+                const SellRef R = J.tsl[q];
+                const MgVals<MIXED> V(R);
+                const int4 h0 = __ldg(R.sl + 2 * s), h1 = __ldg(R.sl + 2 * s + 1);
+                mg_a_group<0, CB, MIXED, T, T2>(R, V, h0.x, h0.y, h1.x, h1.y, Y, n, nn, a, arow, lane, b0, yo, tr, ti);
+                mg_a_group<1, CB, MIXED, T, T2>(R, V, h0.x + h0.y, h0.z, h1.x, h1.y, Y, n, nn, a, arow, lane, b0, yo,
+                                                tr, ti);
+                mg_a_group<2, CB, MIXED, T, T2>(R, V, h0.x + h0.y + h0.z, h0.w, h1.x, h1.z, Y, n, nn, a, arow, lane,
+                                                b0, yo, tr, ti);
+            }
+            {
+                const SellRef R = J.tsl[J.n_td + q];
+                const MgVals<MIXED> V(R);
+                const int sb = b0 >> 5;
+                const int4 h0 = __ldg(R.sl + 2 * sb), h1 = __ldg(R.sl + 2 * sb + 1);
+                mg_b_group<0, CB, MIXED, T, T2>(R, V, h0.x, h0.y, h1.x, h1.y, Y, n, nn, a, arow, b0, yo, tr, ti);
+                mg_b_group<1, CB, MIXED, T, T2>(R, V, h0.x + h0.y, h0.z, h1.x, h1.y, Y, n, nn, a, arow, b0, yo, tr,
+                                                ti);
+                mg_b_group<2, CB, MIXED, T, T2>(R, V, h0.x + h0.y + h0.z, h0.w, h1.x, h1.z, Y, n, nn, a, arow, b0,
+                                                yo, tr, ti);
+            }
+            const double2 f = tdf[q];
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                ar[k] += f.x * tr[k] - f.y * ti[k];
+                ai[k] += f.x * ti[k] + f.y * tr[k];
+            }
+        }
     }
     // sum_c C_c Y C_c^dag
     if (J.cmap) {
@@ -590,11 +629,11 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
     };
     // right-hand side of stage input `in` on every owned entry:
     // post(e, eT, a, b, k_entry)
-    auto rhs_pass = [&](const T2* in, auto&& post) {
+    auto rhs_pass = [&](const T2* in, int slot, auto&& post) {
         for (int u = wg; u < nu; u += W) {
             const int2 us = __ldg(J.units + u);
             T2 r[MG_CB];
-            rhs_unit<MIXED, MG_CB>(J, in, us.x, MG_CB * us.y, lane, r);
+            rhs_unit<MIXED, MG_CB>(J, in, us.x, MG_CB * us.y, lane, r, sh.tdf[slot]);
             const int a = 32 * us.x + lane, b0 = MG_CB * us.y;
 #pragma unroll
             for (int k = 0; k < MG_CB; ++k) {
@@ -613,7 +652,7 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
 #pragma unroll 1
             for (int hb = 0; hb < MG_CB; hb += 2) {
                 double2 r[2];
-                rhs_unit<false, 2>(J, J.y64, us.x, MG_CB * us.y + hb, lane, r);
+                rhs_unit<false, 2, false>(J, J.y64, us.x, MG_CB * us.y + hb, lane, r);
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     const int b = MG_CB * us.y + hb + k;
@@ -649,11 +688,16 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
                 ysb[0][eT] = c;
         }
     });
+    // warp 0 of every block: f_k(tp) into slot 0 (time-dependent terms, FP64)
+    auto publish_td0 = [&](double tp) {
+        if (warp == 0 && lane < J.n_td) sh.tdf[0][lane] = td_coef(J.tf[lane], tp);
+    };
+    publish_td0(J.tlist[0]);
     grid.sync();
     if constexpr (MIXED)
         rhs_pass64([&](size_t e, size_t, int, int, double2 r) { bb[e] = pair_of(r); });
     else
-        rhs_pass(ysb[0], [&](size_t e, size_t, int, int, T2 r) { K(0)[e] = r; });
+        rhs_pass(ysb[0], 0, [&](size_t e, size_t, int, int, T2 r) { K(0)[e] = r; });
 
     // Tr(O_e rho) for rho = src, per-block FP64 partials -> epart[idx][block]
     auto expect_partials = [&](const S* src, int idx) {
@@ -757,9 +801,10 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
             ysb[1][e] = o;
             if (herm && i != j) ysb[1][eT] = t2_conj(o);
         });
+        publish_td0(J.tlist[0] + h0);
         grid.sync();
         float s2 = 0.f;
-        rhs_pass(ysb[1], [&](size_t e, size_t, int i, int j, T2 r) {
+        rhs_pass(ysb[1], 0, [&](size_t e, size_t, int i, int j, T2 r) {
             double2 d = g_to_d2(r);
             if constexpr (!MIXED) {
                 const double2 f0 = g_to_d2(K(0)[e]);
@@ -784,6 +829,7 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
     grid.sync();
 
     auto next_action = [&]() {
+        sh.tnow = t;
         for (;;) {
             if (status != QTL_OK || idx >= J.nt) {
                 sh.action = MG_DONE;
@@ -837,6 +883,11 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
                 const double c2 = hh * tab.c[5 + lane];
                 sh.coef[32 + lane] = c2;
                 sh.coeff[32 + lane] = (float)c2;
+            }
+            // f_k at the stage times t + c_s h (slots 1..6)
+            for (int i = lane; i < 6 * J.n_td; i += 32) {
+                const int st = 1 + i / J.n_td, q = i % J.n_td;
+                sh.tdf[st][q] = td_coef(J.tf[q], sh.tnow + tab.c[st] * hh);
             }
         }
         __syncwarp();
@@ -919,7 +970,7 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
                         mixed_err(e, i, j2, make_float2((float)(r.x - f.x), (float)(r.y - f.y)));
                     });
                 } else {
-                    rhs_pass(in, [&](size_t e, size_t eT, int i, int j2, T2 ks) {
+                    rhs_pass(in, s, [&](size_t e, size_t eT, int i, int j2, T2 ks) {
                         if (s == 6) {
                             bn[e] = pair_add(bb[e], ks);
                             mixed_err(e, i, j2, ks);
@@ -963,7 +1014,7 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
                     });
                 }
             } else {
-                rhs_pass(in, [&](size_t e, size_t eT, int i, int j2, T2 ks) {
+                rhs_pass(in, s, [&](size_t e, size_t eT, int i, int j2, T2 ks) {
                     K(s)[e] = ks;
                     if (s < 6) {
                         // input of stage s+1: y + h sum_{j<=s} a_{s+1,j} k_j

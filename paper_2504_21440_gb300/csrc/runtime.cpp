@@ -533,6 +533,11 @@ static qtl_status ensure_grid(System& s) {
     if (s.units) return QTL_OK;
     if ((st = upload_sell(s.Bt, s.sBt)) != QTL_OK) {
         free_sell(s.sBt);
+    for (DevSell& d : s.sTa) free_sell(d);
+    for (DevSell& d : s.sTb) free_sell(d);
+    free_csr(s.dT);
+    cudaFree(s.d_tf);
+    cudaFree(s.d_tsl);
         return st;
     }
     const int n = s.n, ns = (n + 31) / 32, ncg = (n + 3) / 4;
@@ -546,7 +551,50 @@ static qtl_status ensure_grid(System& s) {
     s.nu_all = (int)(lower.size() + upper.size());
     lower.insert(lower.end(), upper.begin(), upper.end());
     if ((st = upload(&s.units, lower.data(), lower.size())) != QTL_OK) return st;
-    s.herm_h = exactly_hermitian(s.H) ? 1 : 0;
+    bool herm = exactly_hermitian(s.H);
+    for (size_t k = 0; k < s.Htd.size(); ++k)
+        herm = herm && s.ftd[k].kind == QTL_COEF_COS && s.ftd[k].amp_im == 0.0 && exactly_hermitian(s.Htd[k]);
+    s.herm_h = herm ? 1 : 0;
+    if (!s.Htd.empty()) {
+        // -i H_k and (i H_k)^T in sliced ELLPACK, and their references on the device
+        const int ntd = (int)s.Htd.size();
+        s.sTa.resize(ntd);
+        s.sTb.resize(ntd);
+        std::vector<SellRef> refs(2 * ntd);
+        for (int k = 0; k < ntd; ++k) {
+            const Csr& h = s.Htd[k];
+            Csr ta = h, tb;
+            for (int64_t p = 0; p < ta.nnz(); ++p) {   // -i (re + i im) = im - i re
+                const double re = h.re[p], im = h.im[p];
+                ta.re[p] = im;
+                ta.im[p] = -re;
+            }
+            // (i H)^T: row j holds i H[i][j] at column i
+            std::vector<std::vector<std::pair<int32_t, cplx>>> rows(s.n);
+            for (int i = 0; i < s.n; ++i)
+                for (int64_t p = h.rp[i]; p < h.rp[i + 1]; ++p)
+                    rows[h.ci[p]].emplace_back(i, cplx(-h.im[p], h.re[p]));
+            rows_to_csr(s.n, rows, tb);
+            if ((st = upload_sell(ta, s.sTa[k])) != QTL_OK || (st = upload_sell(tb, s.sTb[k])) != QTL_OK)
+                return st;
+        }
+        auto ref = [](const DevSell& d) {
+            SellRef r;
+            r.sl = d.sl;
+            r.desc = d.desc;
+            r.ci = (const int32_t*)d.ci;
+            r.vs64 = d.vs64;
+            r.vs32 = d.vs32;
+            r.vc64 = d.vc64;
+            r.vc32 = d.vc32;
+            return r;
+        };
+        for (int k = 0; k < ntd; ++k) {
+            refs[k] = ref(s.sTa[k]);
+            refs[ntd + k] = ref(s.sTb[k]);
+        }
+        if ((st = upload(&s.d_tsl, refs.data(), refs.size())) != QTL_OK) return st;
+    }
     bool real = true;
     for (const Csr& c : s.C)
         for (double v : c.im) real = real && v == 0.0;
@@ -654,6 +702,9 @@ qtl_status mesolve_grid(System& s, const qtl_c128* state0_dev, int32_t is_ket, c
     J.nu_all = s.nu_all;
     J.herm_h = s.herm_h;
     J.c_real = s.c_real;
+    J.n_td = (int)s.Htd.size();
+    J.tsl = s.d_tsl;
+    J.tf = s.d_tf;
     J.n_c = s.n_c;
     J.crp = s.dC.rp;
     J.cci = s.dC.ci;
@@ -885,6 +936,52 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c, 
     return QTL_OK;
 }
 
+qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f) {
+    if (!sys || !Hk || !f) return QTL_EINVAL;
+    System& s = sys->s;
+    if (s.solved || (int)s.Htd.size() >= QTL_MAX_TD || s.n > 1024) return QTL_EINVAL;
+    if (f->kind != QTL_COEF_COS && f->kind != QTL_COEF_EXP) return QTL_EINVAL;
+    for (double v : {f->amp_re, f->amp_im, f->omega, f->phi, f->t0, f->sigma})
+        if (!std::isfinite(v)) return QTL_EINVAL;
+    if (f->sigma < 0.0) return QTL_EINVAL;
+    Csr h;
+    qtl_status st = to_csr(Hk, s.n, h);
+    if (st != QTL_OK) return st;
+    s.Htd.push_back(h);
+    s.ftd.push_back(*f);
+    // -i H_k stacked row-wise for the trajectory kernel, and the coefficients
+    std::vector<Csr> scaled(s.Htd.size());
+    for (size_t k = 0; k < s.Htd.size(); ++k) {
+        scaled[k] = s.Htd[k];
+        for (int64_t p = 0; p < scaled[k].nnz(); ++p) {
+            const double re = s.Htd[k].re[p], im = s.Htd[k].im[p];
+            scaled[k].re[p] = im;
+            scaled[k].im[p] = -re;
+        }
+    }
+    Csr stacked;
+    stack(scaled, s.n, stacked);
+    free_csr(s.dT);
+    cudaFree(s.d_tf);
+    s.d_tf = nullptr;
+    if ((st = upload_csr(stacked, s.dT)) != QTL_OK || (st = upload(&s.d_tf, s.ftd.data(), s.ftd.size())) != QTL_OK) {
+        s.Htd.pop_back();
+        s.ftd.pop_back();
+        return st;
+    }
+    return QTL_OK;
+}
+
+qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                       const qtl_opts* opts, qtl_c128* expect_out, qtl_stats* stats) {
+    if (!sys || !opts) return QTL_EINVAL;
+    if (sys->s.n_c != 0) return QTL_EINVAL;
+    if (sys->s.n > mc_traj_capacity()) return QTL_ETOOBIG;
+    qtl_opts o = *opts;
+    o.engine = QTL_ENGINE_AUTO;
+    return qtl_mcsolve(sys, psi0, tlist, nt, 1, 0, 0, &o, expect_out, nullptr, stats);
+}
+
 int32_t qtl_system_dim(const qtl_system* sys) { return sys ? sys->s.n : 0; }
 
 int64_t qtl_system_liouvillian_nnz(const qtl_system* sys) { return sys ? sys->s.dL.nnz : 0; }
@@ -908,6 +1005,12 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     if (st != QTL_OK) return st;
     System& s = sys->s;
     if (s.n > 46340) return QTL_ETOOBIG;
+    s.solved = true;
+    if (!s.Htd.empty()) {
+        // time-dependent H: the grid kernel in FP64
+        if (opts->precision != QTL_FP64 || opts->engine == QTL_ENGINE_CLUSTER) return QTL_EINVAL;
+        return mesolve_grid(s, state0_dev, is_ket, tlist_dev, nt, opts, expect_dev, states_dev, info_dev);
+    }
     {
         // engine: the cluster kernel when the problem fits one cluster
         const int64_t L64 = (int64_t)s.n * s.n;
@@ -1017,7 +1120,9 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
     std::vector<Plan> plan(nb);
     for (int b = 0; b < nb; ++b) {
         if (!systems[b] || !state0_dev[b] || (systems[b]->s.n_e > 0 && !expect_dev[b])) return QTL_EINVAL;
+        if (!systems[b]->s.Htd.empty()) return QTL_EINVAL;   // time-dependent H: not on the cluster kernel
         System& s = systems[b]->s;
+        s.solved = true;
         if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
         const int L = s.n * s.n;
         batch_plan(L, &plan[b].C, &plan[b].rpt);
@@ -1249,6 +1354,8 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     if (s.n > mc_wide_capacity()) return QTL_ETOOBIG;
     if (opts->engine == QTL_ENGINE_CLUSTER && s.n > mc_traj_capacity()) return QTL_ETOOBIG;
     const bool wide = s.n > mc_traj_capacity() || opts->engine == QTL_ENGINE_GRID;
+    if (wide && !s.Htd.empty()) return QTL_EINVAL;   // time-dependent terms: trajectory kernel only
+    s.solved = true;
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     const size_t ne = (size_t)s.n_e * nt;
     double2* scratch = nullptr;
@@ -1276,6 +1383,12 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     J.tlist = tlist_dev;
     J.nt = nt;
     J.psi0 = (const double2*)psi0_dev;
+    J.n_td = (int)s.Htd.size();
+    J.tseg = s.dT.seg;
+    J.tci = s.dT.ci;
+    J.tv64 = s.dT.v64;
+    J.tv32 = s.dT.v32;
+    J.tf = s.d_tf;
     J.ntraj = ntraj;
     J.seed = seed;
     J.traj_offset = traj_offset;

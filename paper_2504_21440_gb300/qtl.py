@@ -106,6 +106,10 @@ def load():
     lib.qtl_mesolve_batch.restype = C.c_int
     lib.qtl_mesolve_batch_async.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P]
     lib.qtl_mesolve_batch_async.restype = C.c_int
+    lib.qtl_system_add_td.argtypes = [P, C.POINTER(Op), C.POINTER(Coef)]
+    lib.qtl_system_add_td.restype = C.c_int
+    lib.qtl_sesolve.argtypes = [P, P, P, C.c_int32, C.POINTER(Opts), P, C.POINTER(Stats)]
+    lib.qtl_sesolve.restype = C.c_int
     lib.qtl_batch_create.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P, C.c_int32,
                                      C.POINTER(P)]
     lib.qtl_batch_create.restype = C.c_int
@@ -185,6 +189,18 @@ def _check(status, what):
         raise QtlError(status, what)
 
 
+class Coef(C.Structure):
+    """qtl_coef: f(t) = (amp_re + i amp_im) env(t) g(omega t + phi), g = cos
+    (kind 0) or exp(i .) (kind 1), env a Gaussian around t0 when sigma > 0."""
+    _fields_ = [("kind", C.c_int32), ("amp_re", C.c_double), ("amp_im", C.c_double),
+                ("omega", C.c_double), ("phi", C.c_double), ("t0", C.c_double), ("sigma", C.c_double)]
+
+
+def coef(kind="cos", amp=1.0, omega=0.0, phi=0.0, t0=0.0, sigma=0.0):
+    a = complex(amp)
+    return Coef({"cos": 0, "exp": 1}[kind], a.real, a.imag, float(omega), float(phi), float(t0), float(sigma))
+
+
 class _OpHolder:
     """Keeps the arrays behind a qtl_op alive for the duration of a call."""
 
@@ -221,6 +237,25 @@ def system_create(H, c_ops=(), e_ops=()):
     _check(lib.qtl_system_create(C.byref(hold[0].op), ca, nc, ea, ne, C.byref(out)),
            "qtl_system_create")
     return out
+
+
+def system_add_td(sys, Hk, f):
+    """qtl_system_add_td: adds f(t) Hk (f a Coef, or a dict of coef() arguments)."""
+    h = _OpHolder(Hk)
+    c = f if isinstance(f, Coef) else coef(**f)
+    _check(load().qtl_system_add_td(sys, C.byref(h.op), C.byref(c)), "qtl_system_add_td")
+
+
+def sesolve(sys, n_e, psi0, tlist, opts):
+    """qtl_sesolve with host arrays.  Returns dict(expect[n_e, nt], stats)."""
+    lib = load()
+    p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    ex = np.zeros((max(n_e, 1), len(tl)), dtype=np.complex128)
+    st = Stats()
+    _check(lib.qtl_sesolve(sys, _ptr(p0), _ptr(tl), len(tl), C.byref(opts), _ptr(ex), C.byref(st)),
+           "qtl_sesolve")
+    return dict(expect=ex[:n_e], stats=st.as_dict())
 
 
 def system_free(sys):
@@ -466,14 +501,24 @@ def mcsolve_noalloc(n, a_csr, c_csr, n_c, o_csr, n_e, psi0_dev, tlist_dev, ntraj
 class System:
     """Owning wrapper: System(H, c_ops, e_ops) -> .mesolve(...) / .mcsolve(...)."""
 
-    def __init__(self, H, c_ops=(), e_ops=()):
+    def __init__(self, H, c_ops=(), e_ops=(), td=()):
         self.handle = system_create(H, c_ops, e_ops)
+        try:
+            for Hk, f in td:
+                system_add_td(self.handle, Hk, f)
+        except Exception:
+            system_free(self.handle)
+            self.handle = None
+            raise
         self.n = system_dim(self.handle)
         self.n_e = len(e_ops)
         self.n_c = len(c_ops)
 
     def mesolve(self, state0, tlist, save_states=False, **kw):
         return mesolve(self.handle, self.n_e, state0, tlist, make_opts(**kw), save_states)
+
+    def sesolve(self, psi0, tlist, **kw):
+        return sesolve(self.handle, self.n_e, psi0, tlist, make_opts(**kw))
 
     def mcsolve(self, psi0, tlist, ntraj, seed, traj_offset=0, keep_trajectories=False, **kw):
         return mcsolve(self.handle, self.n_e, psi0, tlist, ntraj, seed, make_opts(**kw),
