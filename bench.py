@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="jc_40x2",
-                    choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc"])
+                    choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc", "optomech_td"])
     ap.add_argument("--rates", default="10,30,100,300")
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -679,8 +679,96 @@ def serving_vs_fp64(qtl, opts_mixed, n_req=40):
             "failed": sum(1 for r in served if r["status"] != 0)}
 
 
+def optomech_system():
+    """The driven optomechanical system of Sec. 3.2 with the paper's
+    parameters: Nc = 10, Nm = 7, wc = 1, wm = 2, g = 0.05, kappa = gamma = 0.01,
+    drive F cos(w_d t)(a + a^dag) with F = 10 kappa and w_d = wc, from the
+    vacuum, tlist = range(0, 5/kappa, 5000), e_ops {a^dag a}."""
+    import scipy.sparse as sp
+    Nc, Nm = 10, 7
+    wc, wm, gc, kap, gam = 1.0, 2.0, 0.05, 0.01, 0.01
+
+    def destroy(N):
+        return sp.diags(np.sqrt(np.arange(1, N)), 1, format="csr", dtype=complex)
+    a = sp.kron(destroy(Nc), sp.identity(Nm), format="csr")
+    b = sp.kron(sp.identity(Nc), destroy(Nm), format="csr")
+    ad, bd = a.conj().T, b.conj().T
+    H0 = (wc * ad @ a + wm * bd @ b + gc / 2 * (a + ad) @ (a + ad) @ (b + bd)).tocsr()
+    drive = ((a + ad).tocsr(), dict(kind="cos", amp=10 * kap, omega=wc))
+    psi0 = np.zeros(Nc * Nm, dtype=complex)
+    psi0[0] = 1
+    tl = np.linspace(0, 5 / kap, 5000)
+    return H0, drive, [np.sqrt(kap) * a, np.sqrt(gam) * b], [(ad @ a).tocsr()], psi0, tl
+
+
+def run_optomech(args):
+    """Time-dependent mesolve: the driven optomechanical system of Sec. 3.2
+    (dimension 70) over t in [0, 500] with 5000 output times, FP64, Tsit5,
+    rtol 1e-8, atol 1e-10, on the grid kernel (the path for time-dependent
+    Hamiltonians).  Value: Lindblad RHS evaluations per second; the oracle
+    (product form, one host core) is timed on the first 2% of the span."""
+    import torch
+    from paper_2504_21440_gb300 import qtl
+    from oracle.timedep import Coef, mesolve_td
+    torch.cuda.set_device(0)
+    qtl.load()
+    dev = torch.device("cuda", 0)
+    H0, drive, c_ops, e_ops, psi0, tl = optomech_system()
+    g = qtl.System(H0, c_ops, e_ops, td=[drive])
+    psi = torch.from_numpy(psi0).to(dev)
+    tld = torch.from_numpy(tl).to(dev)
+    ex = torch.zeros((1, len(tl)), dtype=torch.complex128, device=dev)
+    info = torch.zeros(5, dtype=torch.int64, device=dev)
+    main = torch.cuda.current_stream(dev)
+    o = qtl.make_opts(stream=main.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        qtl.mesolve_async(g.handle, psi, 1, tld, o, ex, None, info)
+        torch.cuda.synchronize(dev)
+    ms = []
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = qtl.launch_count()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        qtl.mesolve_async(g.handle, psi, 1, tld, o, ex, None, info)
+        e1.record(main)
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    launches = qtl.launch_count() - l0
+    inf = info.cpu().numpy()
+    mean_ms = statistics.mean(ms)
+    out = ex.cpu().numpy()
+    # oracle on the first 2% of the span, scaled by RHS evaluations
+    m = 101
+    t0 = time.perf_counter()
+    ref = mesolve_td(H0, [(drive[0], Coef(**drive[1]))], c_ops, e_ops, psi0, tl[:m])
+    t_cpu = time.perf_counter() - t0
+    g.free()
+    print(json.dumps({
+        "metric": "Lindblad RHS evals/s (time-dependent mesolve, driven optomechanics of Sec. 3.2)",
+        "value": int(inf[3]) / (mean_ms / 1e3), "unit": "RHS evals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "optomech_td: Nc=10 x Nm=7, F cos(wd t)(a+a'), t in [0,500], 5000 saveat, FP64",
+                   "l2": "flushed (512 MB write) between timed steps"},
+        "attempted_steps": int(inf[1] + inf[2]), "status": int(inf[0]) & 0xffffffff,
+        "n_final": float(out[0, -1].real),
+        "err_vs_oracle_first_2pct": float(np.max(np.abs(out[0, :m] - ref["expect"][0]))),
+        "cpu_baseline": {"value": ref["stats"]["rhs_evals"] / t_cpu, "unit": "RHS evals/s", "cores": 1,
+                         "kind": "oracle", "sample": "oracle mesolve over the first %d output times (%.1f s)" % (m, t_cpu)},
+        "gpu_launches": launches, "clocks": clk}))
+
+
 def main():
     args = parse()
+    if args.workload == "optomech_td" and args.impl != "reference":
+        run_optomech(args)
+        return
     if args.workload == "serving" and args.impl != "reference":
         run_serving(args)
         return

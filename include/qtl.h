@@ -168,11 +168,12 @@ typedef struct {
  * Terms must be added before the system's first solve (QTL_EINVAL after).
  * Which solvers take them: qtl_sesolve and qtl_mcsolve (trajectories with
  * n <= 1024, FP64 or mixed precision: A(t) = A - i sum_k f_k(t) H_k), and
- * qtl_mesolve / qtl_mesolve_async in FP64 on the grid kernel (the automatic
- * engine picks it; the cluster engine, mixed precision, batches and plans
- * return QTL_EINVAL for such a system).  The grid kernel integrates only the
- * lower triangle of rho when H0 and every H_k are exactly Hermitian and
- * every f_k is real (QTL_COEF_COS with amp_im = 0).
+ * qtl_mesolve / qtl_mesolve_async in FP64 on either engine (the cluster
+ * kernel adds f_k(t) L_k y with L_k = -i (I kron H_k - H_k^T kron I); the
+ * grid kernel adds f_k(t) ((-i H_k) rho + rho (i H_k)) and integrates only
+ * the lower triangle of rho when H0 and every H_k are exactly Hermitian and
+ * every f_k is real, QTL_COEF_COS with amp_im = 0).  Mixed-precision
+ * mesolve, batches and plans return QTL_EINVAL for such a system.
  * Errors: QTL_EINVAL (NULL, bad operator or coefficient, 8 terms already,
  * n > 1024, a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
 qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f);

@@ -114,6 +114,7 @@ struct System {
     std::vector<Csr> Htd;       // time-dependent terms f_k(t) H_k
     std::vector<qtl_coef> ftd;
     DevCsr dT;                  // -i H_k stacked row-wise, segmented (trajectory kernel)
+    DevCsr dTL;                 // their Liouvillians -i (I kron H_k - H_k^T kron I), stacked (cluster kernel)
     std::vector<DevSell> sTa;   // -i H_k in sliced ELLPACK (grid kernel)
     std::vector<DevSell> sTb;   // (i H_k)^T in sliced ELLPACK (grid kernel)
     qtl_coef* d_tf = nullptr;   // device copy of ftd
@@ -130,6 +131,11 @@ struct System {
 // -------------------------------------------- device-side solve descriptors
 struct MeJob {
     int n, L;
+    int n_td;             // time-dependent terms f_k(t) L_k (FP64 single solves)
+    const int32_t* trp;   // L_k = -i (I kron H_k - H_k^T kron I) stacked (rows k*L + r)
+    const int32_t* tci;
+    const double2* tv;
+    const qtl_coef* tf;
     const int4* seg;      // Liouvillian, segmented rows
     const int32_t* ci;
     const double2* lv64;

@@ -36,6 +36,7 @@
 
 #include "internal.h"
 #include "rk.cuh"
+#include "td.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -114,6 +115,8 @@ struct MeShared {
     double h0, d1;
     int action, land, accept, save_idx, repeat_idx;
     int scan[ME_NW];
+    double tnow;                   // the step's start (time-dependent terms)
+    double2 tdf[7][QTL_MAX_TD];    // f_k at t + c_s h (slots 1..6) and at one other time (slot 0)
 };
 
 // Row q of this CTA's cached Liouvillian times the stage input held in the
@@ -238,6 +241,29 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
     uint32_t* s_addr = (uint32_t*)(s_seg + RPT * ME_T);
     TV* s_v = (TV*)(((uintptr_t)(s_addr + J.smem_nnz) + 15) & ~(uintptr_t)15);
     const uint32_t ys_base = smem_addr(s_ys);
+    // sum_k f_k (L_k y)_r for the stage input in buffer offset boff (FP64),
+    // coefficients from slot `slot`; L_k from global memory, its columns
+    // mapped to the owning CTA's stage-input slot on the fly
+    auto td_row = [&](int r, uint32_t boff, int slot) -> double2 {
+        double rx = 0.0, ry = 0.0;
+        for (int q = 0; q < J.n_td; ++q) {
+            double ax = 0.0, ay = 0.0;
+            const int rr = q * L + r;
+            for (int p = __ldg(J.trp + rr); p < __ldg(J.trp + rr + 1); ++p) {
+                const int c = __ldg(J.tci + p);
+                const double2 v = __ldg(J.tv + p);
+                const double2 x = ld_dsmem(
+                    dsmem_map(ys_base + (uint32_t)((c / C) * sizeof(double2)), (uint32_t)(c % C)) + boff,
+                    (double2*)nullptr);
+                ax += v.x * x.x - v.y * x.y;
+                ay += v.x * x.y + v.y * x.x;
+            }
+            const double2 f = sh.tdf[slot][q];
+            rx += f.x * ax - f.y * ay;
+            ry += f.x * ay + f.y * ax;
+        }
+        return make_double2(rx, ry);
+    };
 
     double2 y[RPT], ynew[RPT];
     float2 yf[RPT], yfn[RPT];  // MIXED: FP32 copies, so the stage loop converts nothing
@@ -306,6 +332,8 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             off += sg.w - sg.x;
         }
     }
+    // time-dependent terms: f_k(tlist[0]) for k1 (slot 0)
+    if (warp == 0 && lane < J.n_td) sh.tdf[0][lane] = td_coef(J.tf[lane], J.tlist[0]);
     cl.sync();
 
     // Per-CTA FP64 partials of Tr(O_e rho) over own rows -> J.epart[idx][rank][*].
@@ -399,6 +427,11 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             k[0][m] = k1f[m];
         } else {
             k[0][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, 0u);
+            if (J.n_td > 0) {
+                const double2 d = td_row(row[m], 0u, 0);
+                k[0][m].x += d.x;
+                k[0][m].y += d.y;
+            }
         }
     }
     expect_partials(y, 0);
@@ -452,6 +485,7 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                     make_double2(y[m].x + h0 * f0.x, y[m].y + h0 * f0.y);
             }
         }
+        if (warp == 0 && lane < J.n_td) sh.tdf[0][lane] = td_coef(J.tf[lane], J.tlist[0] + h0);
         cl.sync();
         float s2 = 0.f;
 #pragma unroll
@@ -463,7 +497,12 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 dx = (float)c.x;
                 dy = (float)c.y;
             } else {
-                const double2 f1 = to_d2(spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff));
+                double2 f1 = to_d2(spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff));
+                if (J.n_td > 0) {
+                    const double2 d = td_row(row[m], bufoff, 0);
+                    f1.x += d.x;
+                    f1.y += d.y;
+                }
                 const double2 f0 = to_d2(k[0][m]);
                 dx = (float)(f1.x - f0.x);
                 dy = (float)(f1.y - f0.y);
@@ -485,6 +524,7 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
 
     // thread 0: choose the next action (step / repeated output time / done)
     auto next_action = [&]() {
+        sh.tnow = t;
         for (;;) {
             if (status != QTL_OK || idx >= J.nt) {
                 sh.action = ACT_DONE;
@@ -544,6 +584,11 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 const double cs = hh * tab.c[lane + 5];
                 sh.coef[32 + lane] = cs;
                 sh.coeff[32 + lane] = (float)cs;
+            }
+            // f_k at the stage times t + c_s htry (slots 1..6)
+            for (int i = lane; i < 6 * J.n_td; i += 32) {
+                const int st = 1 + i / J.n_td, q = i % J.n_td;
+                sh.tdf[st][q] = td_coef(J.tf[q], sh.tnow + tab.c[st] * hh);
             }
         }
     };
@@ -637,8 +682,15 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 }
                 cl.sync();
 #pragma unroll
-                for (int m = 0; m < RPT; ++m)
-                    if (own[m]) k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+                for (int m = 0; m < RPT; ++m) {
+                    if (!own[m]) continue;
+                    k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+                    if (J.n_td > 0) {
+                        const double2 d = td_row(row[m], off, s);
+                        k[s][m].x += d.x;
+                        k[s][m].y += d.y;
+                    }
+                }
             }
         }
         // error norm: sum over own rows of (|e| / sc)^2, e = h sum_j e_j k_j

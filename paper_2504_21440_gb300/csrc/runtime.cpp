@@ -536,6 +536,7 @@ static qtl_status ensure_grid(System& s) {
     for (DevSell& d : s.sTa) free_sell(d);
     for (DevSell& d : s.sTb) free_sell(d);
     free_csr(s.dT);
+    free_csr(s.dTL);
     cudaFree(s.d_tf);
     cudaFree(s.d_tsl);
         return st;
@@ -600,6 +601,37 @@ static qtl_status ensure_grid(System& s) {
         for (double v : c.im) real = real && v == 0.0;
     s.c_real = real ? 1 : 0;
     return QTL_OK;
+}
+
+// The Liouvillians of the time-dependent terms alone, L_k = -i (I kron H_k -
+// H_k^T kron I) (column stacking: row i + n j holds -i H_k[i][l] at column
+// l + n j and +i H_k[l][j] at column i + n l), stacked row-wise.
+static qtl_status ensure_td_liouvillian(System& s) {
+    std::lock_guard<std::mutex> lk(g_build_mu);
+    if (s.Htd.empty() || s.dTL.rp) return QTL_OK;
+    const int n = s.n;
+    const int64_t L = (int64_t)n * n;
+    if (L * (int64_t)s.Htd.size() >= (int64_t)INT32_MAX) return QTL_ETOOBIG;
+    std::vector<Csr> parts(s.Htd.size());
+    for (size_t k = 0; k < s.Htd.size(); ++k) {
+        const Csr& h = s.Htd[k];
+        std::vector<std::vector<std::pair<int32_t, cplx>>> ht(n);   // columns of H_k
+        for (int i = 0; i < n; ++i)
+            for (int64_t p = h.rp[i]; p < h.rp[i + 1]; ++p) ht[h.ci[p]].emplace_back(i, at(h, p));
+        std::vector<std::vector<std::pair<int32_t, cplx>>> rows((size_t)L);
+        const cplx mi(0.0, -1.0);
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                auto& r = rows[(size_t)i + (size_t)n * j];
+                for (int64_t p = h.rp[i]; p < h.rp[i + 1]; ++p)
+                    r.emplace_back(h.ci[p] + n * j, mi * at(h, p));
+                for (const auto& lv : ht[j]) r.emplace_back(i + n * lv.first, -mi * lv.second);
+            }
+        rows_to_csr((int)L, rows, parts[k]);
+    }
+    Csr stacked;
+    stack(parts, (int)L, stacked);
+    return upload_csr(stacked, s.dTL);
 }
 
 qtl_status ensure_liouvillian(System& s) {
@@ -1007,9 +1039,9 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     if (s.n > 46340) return QTL_ETOOBIG;
     s.solved = true;
     if (!s.Htd.empty()) {
-        // time-dependent H: the grid kernel in FP64
-        if (opts->precision != QTL_FP64 || opts->engine == QTL_ENGINE_CLUSTER) return QTL_EINVAL;
-        return mesolve_grid(s, state0_dev, is_ket, tlist_dev, nt, opts, expect_dev, states_dev, info_dev);
+        // time-dependent H: FP64 (cluster kernel when it fits, else the grid kernel)
+        if (opts->precision != QTL_FP64) return QTL_EINVAL;
+        if ((st = ensure_td_liouvillian(s)) != QTL_OK) return st;
     }
     {
         // engine: the cluster kernel when the problem fits one cluster
@@ -1068,6 +1100,11 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     J.fixed = opts->fixed_step ? 1 : 0;
     J.method = opts->method;
     J.smem_nnz = (int)need;
+    J.n_td = (int)s.Htd.size();
+    J.trp = s.dTL.rp;
+    J.tci = s.dTL.ci;
+    J.tv = s.dTL.v64;
+    J.tf = s.d_tf;
     QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
     QTL_CUDA(cudaMemcpyAsync(jd, &J, sizeof(J), cudaMemcpyHostToDevice, stream));
     cudaError_t e = launch_me_cluster(jd, 1, L, J.smem_nnz, opts->precision, opts->cluster_size, nullptr, stream);
