@@ -135,35 +135,38 @@ template <class T2, class TV>
 __device__ __forceinline__ T2 mc_spmv_row_s(int r, const int4* __restrict__ s_seg,
                                             const int32_t* __restrict__ s_ci,
                                             const TV* __restrict__ s_v, const T2* x) {
+    // two accumulators (real, imaginary part of the result): on GB300's 1/64
+    // rate FP64 pipe the final additions of split accumulators cost as much
+    // as a row's entries
     const int4 sg = s_seg[r];
-    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
+    decltype(T2::x) ar = 0, ai = 0;
     int p = sg.x;
 #pragma unroll 4
     for (; p < sg.y; ++p) {
         const decltype(T2::x) a = s_v[p].x;
         const T2 xv = x[s_ci[p]];
-        ax = fma(a, xv.x, ax);
-        ay = fma(a, xv.y, ay);
+        ar = fma(a, xv.x, ar);
+        ai = fma(a, xv.y, ai);
     }
 #pragma unroll 4
     for (; p < sg.z; ++p) {
         const decltype(T2::x) b = s_v[p].y;
         const T2 xv = x[s_ci[p]];
-        bx = fma(-b, xv.y, bx);
-        by = fma(b, xv.x, by);
+        ar = fma(-b, xv.y, ar);
+        ai = fma(b, xv.x, ai);
     }
 #pragma unroll 2
     for (; p < sg.w; ++p) {
         const TV a = s_v[p];
         const T2 xv = x[s_ci[p]];
-        ax = fma(a.x, xv.x, ax);
-        ay = fma(a.x, xv.y, ay);
-        bx = fma(-a.y, xv.y, bx);
-        by = fma(a.y, xv.x, by);
+        ar = fma(a.x, xv.x, ar);
+        ai = fma(a.x, xv.y, ai);
+        ar = fma(-a.y, xv.y, ar);
+        ai = fma(a.y, xv.x, ai);
     }
     T2 acc;
-    acc.x = ax + bx;
-    acc.y = ay + by;
+    acc.x = ar;
+    acc.y = ai;
     return acc;
 }
 

@@ -302,7 +302,13 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
 #pragma unroll
                 for (int m = 0; m < RPT; ++m) {
                     if (!own[m]) continue;
+                    // FP64: the sum starts from y (no separate addition on the
+                    // 1/64-rate FP64 pipe); MIXED: FP32 increments added to y after
                     T ax = 0, ay = 0;
+                    if constexpr (!MIXED) {
+                        ax = y[m].x;
+                        ay = y[m].y;
+                    }
 #pragma unroll
                     for (int j = 0; j < 6; ++j) {
                         if (j < s) {
@@ -311,18 +317,19 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                         }
                     }
                     T2 o;
-                    if (s == 6) {
-                        ynew[m] = make_double2(y[m].x + (double)ax, y[m].y + (double)ay);
-                        o = from_d2_mc<T2>(ynew[m]);
-                        if constexpr (MIXED) yfn[m] = o;
-                    } else {
-                        if constexpr (MIXED) {
+                    if constexpr (MIXED) {
+                        if (s == 6) {
+                            ynew[m] = make_double2(y[m].x + (double)ax, y[m].y + (double)ay);
+                            o = from_d2_mc<T2>(ynew[m]);
+                            yfn[m] = o;
+                        } else {
                             o.x = yf[m].x + ax;
                             o.y = yf[m].y + ay;
-                        } else {
-                            o.x = y[m].x + ax;
-                            o.y = y[m].y + ay;
                         }
+                    } else {
+                        o.x = ax;
+                        o.y = ay;
+                        if (s == 6) ynew[m] = make_double2(ax, ay);
                     }
                     ysb[row[m]] = o;
                 }

@@ -126,35 +126,37 @@ template <class T2, class TV>
 __device__ __forceinline__ T2 spmv_dsm(int q, const int4* __restrict__ s_seg,
                                        const uint32_t* __restrict__ s_addr,
                                        const TV* __restrict__ s_v, uint32_t bufoff) {
+    // two accumulators (real and imaginary part): no final additions, which
+    // on the 1/64-rate FP64 pipe cost as much as a short row's entries
     const int4 sg = s_seg[q];
-    decltype(T2::x) ax = 0, ay = 0, bx = 0, by = 0;
+    decltype(T2::x) ar = 0, ai = 0;
     int p = sg.x;
 #pragma unroll 4
     for (; p < sg.y; ++p) {
         const decltype(T2::x) v = s_v[p].x;
         const T2 xv = ld_dsmem(s_addr[p] + bufoff, (T2*)nullptr);
-        ax = fma(v, xv.x, ax);
-        ay = fma(v, xv.y, ay);
+        ar = fma(v, xv.x, ar);
+        ai = fma(v, xv.y, ai);
     }
 #pragma unroll 4
     for (; p < sg.z; ++p) {
         const decltype(T2::x) v = s_v[p].y;
         const T2 xv = ld_dsmem(s_addr[p] + bufoff, (T2*)nullptr);
-        bx = fma(-v, xv.y, bx);
-        by = fma(v, xv.x, by);
+        ar = fma(-v, xv.y, ar);
+        ai = fma(v, xv.x, ai);
     }
 #pragma unroll 2
     for (; p < sg.w; ++p) {
         const TV v = s_v[p];
         const T2 xv = ld_dsmem(s_addr[p] + bufoff, (T2*)nullptr);
-        ax = fma(v.x, xv.x, ax);
-        ay = fma(v.x, xv.y, ay);
-        bx = fma(-v.y, xv.y, bx);
-        by = fma(v.y, xv.x, by);
+        ar = fma(v.x, xv.x, ar);
+        ai = fma(v.x, xv.y, ai);
+        ar = fma(-v.y, xv.y, ar);
+        ai = fma(v.y, xv.x, ai);
     }
     T2 acc;
-    acc.x = ax + bx;
-    acc.y = ay + by;
+    acc.x = ar;
+    acc.y = ai;
     return acc;
 }
 
@@ -663,7 +665,8 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             } else {
 #pragma unroll
                 for (int m = 0; m < RPT; ++m) {
-                    double ax = 0, ay = 0;
+                    // the sum starts from y: no separate FP64 addition
+                    double ax = y[m].x, ay = y[m].y;
 #pragma unroll
                     for (int j = 0; j < 6; ++j) {
                         if (j < s) {
@@ -671,13 +674,8 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                             ay = fma((double)ha[j], (double)k[j][m].y, ay);
                         }
                     }
-                    double2 o;
-                    if (s == 6) {
-                        ynew[m] = make_double2(y[m].x + ax, y[m].y + ay);
-                        o = ynew[m];
-                    } else {
-                        o = make_double2(y[m].x + ax, y[m].y + ay);
-                    }
+                    const double2 o = make_double2(ax, ay);
+                    if (s == 6) ynew[m] = o;
                     ysb[tid + ME_T * m] = o;
                 }
                 cl.sync();
