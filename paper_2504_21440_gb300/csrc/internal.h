@@ -122,6 +122,7 @@ struct System {
     bool solved = false;        // a solve has run: no more terms
     std::vector<int32_t> L_rp;  // host copy of its row pointers (shared-memory sizing)
     double2* ew = nullptr;      // [n*n][n_e] trace weights (built with the Liouvillian)
+    double* odiag = nullptr;    // [n_e][n] diagonals when every observable is real and diagonal
     int32_t* cmap = nullptr;    // [n_c][n] column of C_c's entry in row i, -1 if none
     double2* cval64 = nullptr;  // [n_c][n] its value (only when every row has <= 1 entry)
     float2* cval32 = nullptr;
@@ -227,6 +228,7 @@ struct McJob {
     const int32_t* oci;
     const double2* ov;
     const int4* oseg;     // their row segments (real-only | imaginary-only | complex), or null
+    const double* odiag;  // [n_e][n]: every observable real and diagonal (else null)
     int n_td;             // time-dependent terms f_k(t) (-i H_k), trajectory kernel n <= 1024
     const int4* tseg;     // -i H_k stacked row-wise (rows k*n + r), segmented
     const int32_t* tci;

@@ -129,6 +129,29 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
         // <psi|O_e|psi>/<psi|psi> from the FP64 copy in yd (all rows written and
         // synchronised by the caller); returns |psi|^2 in thread 0.
         auto save = [&](int idx) -> double {
+            if (J.odiag) {
+                // real diagonal observables: <psi|O|psi> = sum_i O_ii |psi_i|^2,
+                // imaginary part exactly 0 (one FMA per observable and row)
+                double p[RPT];
+                double s2 = 0.0;
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    p[m] = own[m] ? y[m].x * y[m].x + y[m].y * y[m].y : 0.0;
+                    s2 += p[m];
+                }
+                red.stage(0, s2);
+                for (int e = 0; e < J.n_e; ++e) {
+                    double sr = 0.0;
+#pragma unroll
+                    for (int m = 0; m < RPT; ++m)
+                        if (own[m]) sr = fma(__ldg(J.odiag + (size_t)e * n + row[m]), p[m], sr);
+                    red.stage(1 + e, sr);
+                }
+                red.finish(1 + J.n_e);
+                if (tid < J.n_e)
+                    J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] = make_double2(bout[1 + tid] / bout[0], 0.0);
+                return bout[0];
+            }
             double s2 = 0.0;
 #pragma unroll
             for (int m = 0; m < RPT; ++m)

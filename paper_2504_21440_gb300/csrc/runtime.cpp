@@ -899,6 +899,7 @@ void qtl_system_free(qtl_system* sys) {
     free_sell(s.sA);
     free_sell(s.sBt);
     cudaFree(s.units);
+    cudaFree(s.odiag);
     cudaFree(s.ew);
     delete sys;
 }
@@ -954,6 +955,23 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c, 
         if ((st = upload(&s.cmap, cmap.data(), cmap.size())) != QTL_OK ||
             (st = upload(&s.cval64, cval64.data(), cval64.size())) != QTL_OK ||
             (st = upload(&s.cval32, cval32.data(), cval32.size())) != QTL_OK) {
+            qtl_system_free(sys);
+            return st;
+        }
+    }
+    // observables that are real and diagonal (number operators, sigma_z,
+    // projectors): their diagonals, for the trajectory kernel's saves
+    bool rdiag = s.n_e > 0;
+    for (const Csr& o : s.O)
+        for (int i = 0; i < s.n && rdiag; ++i)
+            for (int64_t p = o.rp[i]; p < o.rp[i + 1] && rdiag; ++p)
+                if (o.ci[p] != i || o.im[p] != 0.0) rdiag = false;
+    if (rdiag) {
+        std::vector<double> d((size_t)s.n_e * s.n, 0.0);
+        for (int e = 0; e < s.n_e; ++e)
+            for (int i = 0; i < s.n; ++i)
+                for (int64_t p = s.O[e].rp[i]; p < s.O[e].rp[i + 1]; ++p) d[(size_t)e * s.n + i] += s.O[e].re[p];
+        if ((st = upload(&s.odiag, d.data(), d.size())) != QTL_OK) {
             qtl_system_free(sys);
             return st;
         }
@@ -1417,6 +1435,7 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     J.oci = s.dO.ci;
     J.ov = s.dO.v64;
     J.oseg = s.dO.seg;
+    J.odiag = s.odiag;
     J.tlist = tlist_dev;
     J.nt = nt;
     J.psi0 = (const double2*)psi0_dev;
