@@ -302,6 +302,12 @@ void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, con
                  int is_ket, double* epart, qtl_c128* expect_dev, qtl_device_info* info_dev,
                  const qtl_opts* opts, int smem_nnz);
 
+// Stream-ordered allocation from the library's own pool on the current
+// device.  The pool keeps up to 16 GiB of freed memory for reuse instead
+// of returning it to the driver at every synchronisation,
+// which the default pool does: repeated solves then map no new memory.
+cudaError_t qtl_malloc_async(void** p, size_t bytes, cudaStream_t st);
+
 void count_launch(int k = 1);
 void set_cuda_error(cudaError_t e);
 

@@ -23,6 +23,32 @@ static std::atomic<long long> g_launches{0};
 static thread_local std::string g_cuda_err;
 
 void count_launch(int k) { g_launches += k; }
+
+cudaError_t qtl_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            if ((e = cudaMemPoolCreate(&np, &props)) != cudaSuccess) return e;
+            unsigned long long thr = 16ull << 30;
+            cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &thr);
+            pools[dev] = np;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 void set_cuda_error(cudaError_t e) {
     g_cuda_err = std::string(cudaGetErrorName(e)) + ": " + cudaGetErrorString(e);
 }
@@ -711,7 +737,7 @@ qtl_status mesolve_grid(System& s, const qtl_c128* state0_dev, int32_t is_ket, c
     const bool mixed = opts->precision == QTL_MIXED;
     const size_t b_base = mixed ? up(2 * L * sizeof(float4)) : 0, b_y64 = mixed ? up(L * sizeof(double2)) : 0;
     char* scratch = nullptr;
-    QTL_CUDA(cudaMallocAsync((void**)&scratch, 2 * b_y + b_k + b_ys + b_err + b_ep + b_base + b_y64, stream));
+    QTL_CUDA(qtl_malloc_async((void**)&scratch, 2 * b_y + b_k + b_ys + b_err + b_ep + b_base + b_y64, stream));
     MgJob J;
     std::memset(&J, 0, sizeof(J));
     J.n = s.n;
@@ -1089,7 +1115,7 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     char* scratch = nullptr;
     const size_t epart_bytes = (size_t)nt * C * 2 * (s.n_e > 0 ? s.n_e : 1) * sizeof(double);
     const size_t bytes = epart_bytes + sizeof(MeJob) + 512;
-    QTL_CUDA(cudaMallocAsync((void**)&scratch, bytes, stream));
+    QTL_CUDA(qtl_malloc_async((void**)&scratch, bytes, stream));
     MeJob J;
     std::memset(&J, 0, sizeof(J));
     J.n = s.n;
@@ -1211,7 +1237,7 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
     }
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     char* scratch = nullptr;
-    QTL_CUDA(cudaMallocAsync((void**)&scratch, off, stream));
+    QTL_CUDA(qtl_malloc_async((void**)&scratch, off, stream));
     std::vector<MeJob> jobs(nb);
     std::vector<int> first(nk + 1, 0);
     int q = 0;
@@ -1302,7 +1328,7 @@ extern "C" qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb,
     }
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     char* buf = nullptr;
-    QTL_CUDA(cudaMallocAsync((void**)&buf, off, stream));
+    QTL_CUDA(qtl_malloc_async((void**)&buf, off, stream));
     std::vector<const qtl_c128*> sd(nb);
     std::vector<qtl_c128*> ed(nb);
     QTL_CUDA(cudaMemcpyAsync(buf + tl_off, tlist, (size_t)nt * 8, cudaMemcpyHostToDevice, stream));
@@ -1355,7 +1381,7 @@ qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket, 
     char* buf = nullptr;
     const size_t bytes = n0 * 16 + (size_t)nt * 8 + ne * 16 + (states_out ? (size_t)nt * L * 16 : 0) +
                          sizeof(qtl_device_info) + 5 * 256;
-    QTL_CUDA(cudaMallocAsync((void**)&buf, bytes, stream));
+    QTL_CUDA(qtl_malloc_async((void**)&buf, bytes, stream));
     size_t off = 0;
     auto carve = [&](size_t b) {
         char* p = buf + off;
@@ -1415,7 +1441,7 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     const size_t ne = (size_t)s.n_e * nt;
     double2* scratch = nullptr;
     if (!traj_expect_dev && ne > 0) {
-        QTL_CUDA(cudaMallocAsync((void**)&scratch, ne * ntraj * sizeof(double2), stream));
+        QTL_CUDA(qtl_malloc_async((void**)&scratch, ne * ntraj * sizeof(double2), stream));
     }
     McJob J;
     std::memset(&J, 0, sizeof(J));
@@ -1482,7 +1508,7 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
         McWidePlan plan;
         void* wscr = nullptr;
         e = mc_wide_plan(J, opts->precision, &plan);
-        if (e == cudaSuccess && cudaMallocAsync(&wscr, plan.scratch_bytes, stream) != cudaSuccess) {
+        if (e == cudaSuccess && qtl_malloc_async(&wscr, plan.scratch_bytes, stream) != cudaSuccess) {
             cudaGetLastError();
             if (scratch) cudaFreeAsync(scratch, stream);
             return QTL_ENOMEM;
@@ -1517,7 +1543,7 @@ qtl_status qtl_mcsolve(qtl_system* sys, const qtl_c128* psi0, const double* tlis
     char* buf = nullptr;
     const size_t bytes = (size_t)s.n * 16 + (size_t)nt * 8 + ne * 16 + ne * ntraj * 16 +
                          sizeof(qtl_device_info) + 5 * 256;
-    QTL_CUDA(cudaMallocAsync((void**)&buf, bytes, stream));
+    QTL_CUDA(qtl_malloc_async((void**)&buf, bytes, stream));
     size_t off = 0;
     auto carve = [&](size_t b) {
         char* p = buf + off;

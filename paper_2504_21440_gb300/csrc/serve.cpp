@@ -115,7 +115,7 @@ static void srv_admit(qtl_server* S, SrvReq* q, int slot) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t o_st = 0, o_tl = up(n0 * 16), o_ex = o_tl + up(nt * 8), o_inf = o_ex + up(q->ex_bytes + 16);
     const size_t total = o_inf + 256;
-    if (stt == QTL_OK && cudaMallocAsync((void**)&dbuf, total, st) != cudaSuccess) stt = QTL_ENOMEM;
+    if (stt == QTL_OK && qtl_malloc_async((void**)&dbuf, total, st) != cudaSuccess) stt = QTL_ENOMEM;
     if (stt == QTL_OK) {
         cudaMemcpyAsync(dbuf + o_st, q->r.state0, n0 * 16, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(dbuf + o_tl, q->r.tlist, nt * 8, cudaMemcpyHostToDevice, st);
