@@ -19,6 +19,8 @@ step after the paper:
   mcsolve.py   Monte-Carlo wave-function method (Sec. 3.3)
   timedep.py   time-dependent Hamiltonians H0 + sum_k f_k(t) H_k (Sec. 2,
                Sec. 3.2) for mesolve and mcsolve; sesolve (Sec. 3.1)
+  stochastic.py  the stochastic Schroedinger equation under homodyne
+               detection (Sec. 3.4), Euler-Maruyama with renormalisation
 
 Parity status: every function here is pinned by tests/test_oracle_*.py to
 closed forms, brute-force matrix exponentials, invariants, order conditions
