@@ -246,6 +246,27 @@ qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb, const qtl_c
 qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
                        const qtl_opts* opts, qtl_c128* expect_out, qtl_stats* stats);
 
+/* ssesolve (Sec. 3.4): the stochastic Schroedinger equation under homodyne
+ * detection, in Ito form d psi = -i K psi dt + sum_n M_n psi dW_n with
+ * K = H + i sum_n (e_n/2 S_n - 1/2 S_n^dag S_n - e_n^2/8), M_n = S_n - e_n/2,
+ * e_n = <psi|S_n + S_n^dag|psi>; the homodyne current is J_n = e_n + dW_n/dt.
+ * The system's collapse operators are the stochastic operators S_n (1 to 4);
+ * time-dependent terms are not taken (QTL_EINVAL).  n <= 1024 (QTL_ETOOBIG).
+ * Integration: Euler-Maruyama with the fixed step opts->dt_fixed
+ * (opts->fixed_step must be 1, precision FP64; else QTL_EINVAL), each step
+ * clamped to land on tlist, the state renormalised after every step.
+ * dW_n = sqrt(h) z with z standard normal by the Box-Muller transform of
+ * draws 2j and 2j + 1 (j = step * n_sc + n) of trajectory j's Philox stream
+ * (counter (draw, trajectory, 0, 0), key from seed); trajectories 0..ntraj-1.
+ *   expect_out[n_e*nt]: trajectory mean of <psi|O_k|psi>/<psi|psi>;
+ *   meas_out[n_c*nt]:   trajectory mean of J_n of the last step ending at or
+ *                       before each time (e_n(psi0) at tlist[0]).
+ * Host pointers; returns when done; stats->steps_acc = steps over all
+ * trajectories. */
+qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                        int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
+                        double* meas_out, qtl_stats* stats);
+
 /* Reusable batch plan (Sec. 3.2 over nb independent systems, as
  * qtl_mesolve_batch_async), built once and replayed.
  *   qtl_batch_create: the same arguments as qtl_mesolve_batch_async (device

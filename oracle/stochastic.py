@@ -20,8 +20,8 @@ Readings where the paper is silent (the library implements the same):
     Box-Muller transform (Box & Muller, 1958) of two uniforms of the
     trajectory's Philox stream: draws 2j and 2j + 1 with
     j = step * n_sc + n give u1, u2 and z = sqrt(-2 ln u1) cos(2 pi u2);
-  * recorded at every tlist time t_i: <psi|O|psi>/<psi|psi> and, for i >= 1,
-    J_n of the step that ends at t_i (at t_0: e_n(psi0));
+  * recorded at every tlist time t_i: <psi|O|psi>/<psi|psi> and J_n of the
+    last step that ended at or before t_i (at t_0: e_n(psi0));
   * ensemble outputs are arithmetic means over trajectories.
 """
 import math
@@ -64,9 +64,9 @@ def sse_trajectory(H, sc_ops, e_ops, psi0, tlist, dt, seed, traj):
     save(0, e0)
     t = float(tlist[0])
     step = 0
+    js = e0
     for idx in range(1, len(tlist)):
         t_target = float(tlist[idx])
-        js = e0
         while t < t_target:
             land = dt >= (t_target - t) - LAND_ULPS * 2.0 ** -52 * max(1.0, abs(t_target))
             h = (t_target - t) if land else dt

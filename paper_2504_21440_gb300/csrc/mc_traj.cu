@@ -742,6 +742,13 @@ cudaError_t launch_mc_traj(const McJob& J0, int precision, cudaStream_t st) {
     return precision == QTL_MIXED ? mc_dispatch<true>(J, sh, st) : mc_dispatch<false>(J, sh, st);
 }
 
+cudaError_t launch_traj_mean(const double2* traj, double2* out, int nrows, int ntraj, cudaStream_t st) {
+    if (nrows == 0) return cudaSuccess;
+    count_launch();
+    mc_reduce_kernel<<<nrows < 4096 ? nrows : 4096, 256, 0, st>>>(traj, out, nrows, ntraj);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mc_reduce(const McJob& J, cudaStream_t st) {
     int nrows = J.n_e * J.nt;
     if (nrows == 0) return cudaSuccess;

@@ -1058,6 +1058,85 @@ qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlis
     return qtl_mcsolve(sys, psi0, tlist, nt, 1, 0, 0, &o, expect_out, nullptr, stats);
 }
 
+qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt, int32_t ntraj,
+                        uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out, double* meas_out,
+                        qtl_stats* stats) {
+    if (!sys || !psi0 || !tlist || nt < 1 || ntraj < 1 || !meas_out) return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    if (!opts->fixed_step || opts->precision != QTL_FP64) return QTL_EINVAL;
+    System& s = sys->s;
+    if (s.n_c < 1 || s.n_c > SSE_MAXSC || !s.Htd.empty()) return QTL_EINVAL;
+    if (s.n_e > 0 && !expect_out) return QTL_EINVAL;
+    if (s.n > 1024) return QTL_ETOOBIG;
+    if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    for (int i = 0; i < s.n; ++i)
+        if (!finite_c(psi0[i])) return QTL_EINVAL;
+    s.solved = true;
+    const size_t n = (size_t)s.n, ne = (size_t)s.n_e * nt, nm = (size_t)s.n_c * nt;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = (off + b + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_psi = take(n * 16), o_tl = take((size_t)nt * 8), o_te = take(ne * ntraj * 16),
+                 o_tm = take(nm * ntraj * 16), o_ex = take(ne * 16), o_ms = take(nm * 16),
+                 o_inf = take(sizeof(qtl_device_info));
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    char* buf = nullptr;
+    QTL_CUDA(qtl_malloc_async((void**)&buf, off, stream));
+    McJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.n = s.n;
+    J.aseg = s.dA.seg;
+    J.aci = s.dA.ci;
+    J.av64 = s.dA.v64;
+    J.n_c = s.n_c;
+    J.crp = s.dC.rp;
+    J.cci = s.dC.ci;
+    J.cv = s.dC.v64;
+    J.n_e = s.n_e;
+    J.orp = s.dO.rp;
+    J.oci = s.dO.ci;
+    J.ov = s.dO.v64;
+    J.tlist = (const double*)(buf + o_tl);
+    J.nt = nt;
+    J.psi0 = (const double2*)(buf + o_psi);
+    J.ntraj = ntraj;
+    J.seed = seed;
+    J.traj_expect = (double2*)(buf + o_te);
+    J.expect = (double2*)(buf + o_ex);
+    J.traj_meas = (double2*)(buf + o_tm);
+    J.meas = (double2*)(buf + o_ms);
+    J.info = (qtl_device_info*)(buf + o_inf);
+    J.dt_fixed = opts->dt_fixed;
+    cudaError_t e;
+    std::vector<qtl_c128> mh(nm);
+    qtl_device_info info;
+    std::memset(&info, 0, sizeof(info));
+    if ((e = cudaMemcpyAsync(buf + o_psi, psi0, n * 16, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_tl, tlist, (size_t)nt * 8, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(buf + o_inf, 0, sizeof(qtl_device_info), stream)) != cudaSuccess ||
+        (e = launch_sse_traj(J, stream)) != cudaSuccess ||
+        (ne > 0 && (e = cudaMemcpyAsync(expect_out, buf + o_ex, ne * 16, cudaMemcpyDeviceToHost, stream)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(mh.data(), buf + o_ms, nm * 16, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&info, buf + o_inf, sizeof(info), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) {
+        set_cuda_error(e);
+        cudaFreeAsync(buf, stream);
+        cudaStreamSynchronize(stream);
+        return QTL_ECUDA;
+    }
+    cudaFreeAsync(buf, stream);
+    QTL_CUDA(cudaStreamSynchronize(stream));
+    for (size_t i = 0; i < nm; ++i) meas_out[i] = mh[i].re;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->steps_acc = info.steps_acc;
+    }
+    return QTL_OK;
+}
+
 int32_t qtl_system_dim(const qtl_system* sys) { return sys ? sys->s.n : 0; }
 
 int64_t qtl_system_liouvillian_nnz(const qtl_system* sys) { return sys ? sys->s.dL.nnz : 0; }

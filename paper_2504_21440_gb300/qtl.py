@@ -110,6 +110,9 @@ def load():
     lib.qtl_system_add_td.restype = C.c_int
     lib.qtl_sesolve.argtypes = [P, P, P, C.c_int32, C.POINTER(Opts), P, C.POINTER(Stats)]
     lib.qtl_sesolve.restype = C.c_int
+    lib.qtl_ssesolve.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(Opts), P, P,
+                                 C.POINTER(Stats)]
+    lib.qtl_ssesolve.restype = C.c_int
     lib.qtl_batch_create.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P, C.c_int32,
                                      C.POINTER(P)]
     lib.qtl_batch_create.restype = C.c_int
@@ -256,6 +259,20 @@ def sesolve(sys, n_e, psi0, tlist, opts):
     _check(lib.qtl_sesolve(sys, _ptr(p0), _ptr(tl), len(tl), C.byref(opts), _ptr(ex), C.byref(st)),
            "qtl_sesolve")
     return dict(expect=ex[:n_e], stats=st.as_dict())
+
+
+def ssesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts):
+    """qtl_ssesolve with host arrays.  Returns dict(expect[n_e, nt],
+    measurement[n_sc, nt], stats)."""
+    lib = load()
+    p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    ex = np.zeros((max(n_e, 1), len(tl)), dtype=np.complex128)
+    ms = np.zeros((max(n_sc, 1), len(tl)), dtype=np.float64)
+    st = Stats()
+    _check(lib.qtl_ssesolve(sys, _ptr(p0), _ptr(tl), len(tl), int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
+                            C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st)), "qtl_ssesolve")
+    return dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict())
 
 
 def system_free(sys):
@@ -516,6 +533,10 @@ class System:
 
     def mesolve(self, state0, tlist, save_states=False, **kw):
         return mesolve(self.handle, self.n_e, state0, tlist, make_opts(**kw), save_states)
+
+    def ssesolve(self, psi0, tlist, ntraj, seed, **kw):
+        """The collapse operators given at construction are the stochastic operators."""
+        return ssesolve(self.handle, self.n_e, self.n_c, psi0, tlist, ntraj, seed, make_opts(**kw))
 
     def sesolve(self, psi0, tlist, **kw):
         return sesolve(self.handle, self.n_e, psi0, tlist, make_opts(**kw))
