@@ -20,8 +20,11 @@ def destroy(N):
 
 
 def coherent(N, alpha):
-    n = np.arange(N)
-    v = np.exp(-abs(alpha) ** 2 / 2) * alpha ** n / np.sqrt([math.factorial(int(k)) for k in n])
+    # c_k = e^{-|alpha|^2/2} alpha^k / sqrt(k!), by the recurrence c_k = c_{k-1} alpha / sqrt(k)
+    v = np.zeros(N, dtype=complex)
+    v[0] = np.exp(-abs(alpha) ** 2 / 2)
+    for k in range(1, N):
+        v[k] = v[k - 1] * alpha / math.sqrt(k)
     return v / np.linalg.norm(v)
 
 
@@ -85,3 +88,24 @@ def test_ssesolve_refuses_bad_arguments():
     g2.free()
     for e in (e1, e2, e3):
         assert e.value.status == qtl.QTL_EINVAL
+
+
+@pytest.mark.parametrize("N", [300, 600], ids=["rows2", "rows4"])
+def test_ssesolve_two_and_four_rows_per_thread(N):
+    """Dimensions above 256 take 2 and 4 rows per thread: parity with the
+    oracle over a short horizon."""
+    qtl = require_gpu()
+    a = destroy(N)
+    H = (1.3 * (a.conj().T @ a) + 0.2 * (a + a.conj().T)).tocsr()
+    sc = [math.sqrt(0.7) * a]
+    e_ops = [a, (a.conj().T @ a).tocsr()]
+    psi0 = coherent(N, 1.5 - 0.5j)
+    tl = np.linspace(0, 0.04, 3)
+    g = qtl.System(H, sc, e_ops)
+    try:
+        got = g.ssesolve(psi0, tl, 2, 9, fixed_dt=0.002)
+    finally:
+        g.free()
+    ref = o_ssesolve(H, sc, e_ops, psi0, tl, 0.002, 2, 9)
+    assert np.max(np.abs(got["expect"] - ref["expect"])) <= 1e-10
+    assert np.max(np.abs(got["measurement"] - ref["measurement"])) <= 1e-8

@@ -188,3 +188,26 @@ def test_time_dependent_systems_refuse_unsupported_paths():
     g.free()
     for e in (e1, e3, e4, e5):
         assert e.value.status == qtl.QTL_EINVAL
+
+
+@pytest.mark.parametrize("N", [300, 600], ids=["rows2", "rows4"])
+def test_mcsolve_td_two_and_four_rows_per_thread(N):
+    """Time-dependent trajectories above 256 rows (2 and 4 rows per thread)
+    against the oracle at fixed steps, trajectory by trajectory."""
+    qtl = require_gpu()
+    a = destroy(N)
+    H0 = (0.9 * (a.conj().T @ a)).tocsr()
+    spec = [((a + a.conj().T).tocsr(), dict(kind="cos", amp=0.6, omega=1.1, sigma=0.5, t0=0.1))]
+    ot, lt = both(spec)
+    c_ops = [math.sqrt(0.3) * a]
+    e_ops = [a, (a.conj().T @ a).tocsr()]
+    psi0 = np.zeros(N, dtype=complex)
+    psi0[3] = 1
+    tl = np.linspace(0, 0.2, 3)
+    g = qtl.System(H0, c_ops, e_ops, td=lt)
+    try:
+        got = g.mcsolve(psi0, tl, 3, 17, keep_trajectories=True, fixed_dt=0.01)
+    finally:
+        g.free()
+    ref = mcsolve_td(H0, ot, c_ops, e_ops, psi0, tl, 3, 17, fixed_dt=0.01, keep_trajectories=True)
+    assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-9
