@@ -246,6 +246,9 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
     // sum_k f_k (L_k y)_r for the stage input in buffer offset boff (FP64),
     // coefficients from slot `slot`; L_k from global memory, its columns
     // mapped to the owning CTA's stage-input slot on the fly
+    // (a power-of-two cluster, the usual case, maps a column with shifts)
+    const bool c_pow2 = (C & (C - 1)) == 0;
+    const int c_lg = __ffs(C) - 1;
     auto td_row = [&](int r, uint32_t boff, int slot) -> double2 {
         double rx = 0.0, ry = 0.0;
         for (int q = 0; q < J.n_td; ++q) {
@@ -254,9 +257,10 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             for (int p = __ldg(J.trp + rr); p < __ldg(J.trp + rr + 1); ++p) {
                 const int c = __ldg(J.tci + p);
                 const double2 v = __ldg(J.tv + p);
+                const uint32_t slot_c = c_pow2 ? (uint32_t)(c >> c_lg) : (uint32_t)(c / C);
+                const uint32_t rank_c = c_pow2 ? (uint32_t)(c & (C - 1)) : (uint32_t)(c % C);
                 const double2 x = ld_dsmem(
-                    dsmem_map(ys_base + (uint32_t)((c / C) * sizeof(double2)), (uint32_t)(c % C)) + boff,
-                    (double2*)nullptr);
+                    dsmem_map(ys_base + slot_c * (uint32_t)sizeof(double2), rank_c) + boff, (double2*)nullptr);
                 ax += v.x * x.x - v.y * x.y;
                 ay += v.x * x.y + v.y * x.x;
             }
