@@ -101,3 +101,73 @@ def ssesolve(H, sc_ops, e_ops, psi0, tlist, dt, ntraj, seed, keep_trajectories=F
         out["traj_expect"] = ex
         out["traj_measurement"] = ms
     return out
+
+
+def sme_trajectory(H, c_ops, sc_ops, e_ops, rho0, tlist, dt, seed, traj):
+    """One trajectory of the stochastic master equation of Sec. 3.4,
+        d rho = -i[H, rho] dt + sum_i D[C_i] rho dt + sum_n D[S_n] rho dt
+                + sum_n H[S_n] rho dW_n,
+        H[O] rho = O rho + rho O^dag - Tr(O rho + rho O^dag) rho,
+    with J_n = Tr(S_n rho + rho S_n^dag) + dW_n/dt.  Euler-Maruyama with the
+    steps, landing and Wiener increments of sse_trajectory; no
+    renormalisation (the scheme keeps Tr rho = 1 up to rounding, since
+    Tr H[S] rho = 0 at unit trace).  Returns (expect[k, t], measurement[n, t])."""
+    from .lindblad import lindblad_rhs
+    S = [np.asarray(sp.csr_matrix(s, dtype=np.complex128).todense()) for s in sc_ops]
+    C = [sp.csr_matrix(c, dtype=np.complex128) for c in list(c_ops) + list(sc_ops)]
+    Hm = sp.csr_matrix(H, dtype=np.complex128)
+    nsc = len(S)
+    rho = np.array(rho0, dtype=np.complex128)
+    tlist = np.asarray(tlist, dtype=np.float64)
+    expect = np.zeros((len(e_ops), len(tlist)), dtype=np.complex128)
+    meas = np.zeros((nsc, len(tlist)))
+
+    def hom(Sn, r):
+        v = Sn @ r + r @ Sn.conj().T
+        return v, float(np.trace(v).real)
+
+    def save(idx, js):
+        for k, O in enumerate(e_ops):
+            expect[k, idx] = np.trace(np.asarray(O @ rho))
+        meas[:, idx] = js
+
+    js = [hom(s, rho)[1] for s in S]
+    save(0, js)
+    t = float(tlist[0])
+    step = 0
+    for idx in range(1, len(tlist)):
+        t_target = float(tlist[idx])
+        while t < t_target:
+            land = dt >= (t_target - t) - LAND_ULPS * 2.0 ** -52 * max(1.0, abs(t_target))
+            h = (t_target - t) if land else dt
+            dW = [math.sqrt(h) * normal(seed, traj, step * nsc + n) for n in range(nsc)]
+            new = rho + h * np.asarray(lindblad_rhs(Hm, C, rho))
+            trs = []
+            for n in range(nsc):
+                v, tr = hom(S[n], rho)
+                trs.append(tr)
+                new = new + dW[n] * (v - tr * rho)
+            rho = new
+            js = [trs[n] + dW[n] / h for n in range(nsc)]
+            t = t_target if land else t + h
+            step += 1
+        save(idx, js)
+    return expect, meas
+
+
+def smesolve(H, c_ops, sc_ops, e_ops, state0, tlist, dt, ntraj, seed, keep_trajectories=False):
+    """Ensemble of SME trajectories 0..ntraj-1 from a ket or a density matrix.
+    Returns dict(expect, measurement, traj_expect?, traj_measurement?)."""
+    st = np.asarray(state0, dtype=np.complex128)
+    rho0 = np.outer(st, st.conj()) if st.ndim == 1 else st
+    ex, ms = [], []
+    for j in range(ntraj):
+        a, b = sme_trajectory(H, c_ops, sc_ops, e_ops, rho0, tlist, dt, seed, j)
+        ex.append(a)
+        ms.append(b)
+    ex, ms = np.array(ex), np.array(ms)
+    out = dict(expect=ex.mean(axis=0), measurement=ms.mean(axis=0))
+    if keep_trajectories:
+        out["traj_expect"] = ex
+        out["traj_measurement"] = ms
+    return out

@@ -72,3 +72,53 @@ def test_dephasing_monitor_ensemble_rate():
     assert np.all(np.abs(r["expect"][0].real - np.exp(-2 * g * tl)) <= tol)
     sdz = r["traj_expect"][:, 1, :].real.std(axis=0)
     assert np.all(np.abs(r["expect"][1].real) <= 4 * sdz / math.sqrt(600) + 0.01)
+
+
+from oracle.stochastic import sme_trajectory, smesolve  # noqa: E402
+
+
+def test_sme_without_measurement_is_euler_on_lindblad():
+    """No measured operator: explicit Euler on the master equation; for a
+    decaying two-level system the excited population is (1 - g h)^k."""
+    g, dt = 0.8, 0.01
+    sm = np.array([[0, 0], [1, 0]], dtype=complex)
+    tl = np.linspace(0, 1, 6)
+    ex, ms = sme_trajectory(np.zeros((2, 2)), [math.sqrt(g) * sm], [], [np.diag([1.0, 0.0]).astype(complex)],
+                            np.diag([1.0, 0.0]).astype(complex), tl, dt, 1, 0)
+    k = 20 * np.arange(6)
+    assert np.max(np.abs(ex[0] - (1 - g * dt) ** k)) <= 1e-12
+
+
+def test_sme_homodyne_keeps_a_coherent_state():
+    """S = sqrt(k) a on a damped cavity: H[S] maps |a><a| to a multiple of
+    itself with zero trace, so every trajectory keeps <a> = alpha(t) up to
+    the scheme's O(dt) error."""
+    N, w, kap, a0 = 16, 1.0, 0.5, 1.0 + 0.5j
+    a = sp.diags(np.sqrt(np.arange(1, N)), 1, format="csr", dtype=complex)
+    v = np.zeros(N, dtype=complex)
+    v[0] = math.exp(-abs(a0) ** 2 / 2)
+    for q in range(1, N):
+        v[q] = v[q - 1] * a0 / math.sqrt(q)
+    v /= np.linalg.norm(v)
+    tl = np.linspace(0, 1, 6)
+    al = a0 * np.exp(-(1j * w + kap / 2) * tl)
+    for traj in range(2):
+        ex, ms = sme_trajectory(w * (a.conj().T @ a), [], [math.sqrt(kap) * a], [a], np.outer(v, v.conj()),
+                                tl, 1e-3, 5, traj)
+        assert np.max(np.abs(ex[0] - al)) <= 5e-3
+
+
+def test_sme_ensemble_mean_is_euler_on_lindblad():
+    """Given rho_k the Euler-Maruyama step's noise term has zero mean, and the
+    master equation is linear, so the ensemble mean follows explicit Euler on
+    the master equation: monitored dephasing S = sqrt(g) sz on |+> gives
+    E<sx> = (1 - 2 g h)^k within the sampling error."""
+    g, dt = 0.5, 0.01
+    SZ_ = np.diag([1.0, -1.0]).astype(complex)
+    SX_ = np.array([[0, 1], [1, 0]], dtype=complex)
+    tl = np.linspace(0, 1, 3)
+    r = smesolve(np.zeros((2, 2)), [], [math.sqrt(g) * SZ_], [SX_], np.array([1, 1]) / math.sqrt(2), tl, dt,
+                 400, 13, keep_trajectories=True)
+    sd = r["traj_expect"][:, 0, :].real.std(axis=0)
+    k = 50 * np.arange(3)
+    assert np.all(np.abs(r["expect"][0].real - (1 - 2 * g * dt) ** k) <= 4 * sd / math.sqrt(400) + 1e-12)
