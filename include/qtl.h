@@ -267,6 +267,24 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
                         int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
                         double* meas_out, qtl_stats* stats);
 
+/* smesolve (Sec. 3.4): the stochastic master equation under homodyne
+ * detection, in Ito form
+ *   d rho = -i[H, rho] dt + sum_i D[C_i] rho dt + sum_n D[S_n] rho dt
+ *           + sum_n H[S_n] rho dW_n,
+ *   H[S] rho = S rho + rho S^dag - Tr(S rho + rho S^dag) rho,
+ * with homodyne currents J_n = Tr(S_n rho + rho S_n^dag) + dW_n/dt.  The
+ * system's last n_sc collapse operators (1 to 4) are the measured S_n, the
+ * others the unmeasured C_i.  rho0 = |psi0><psi0|; n*n <= 4096
+ * (QTL_ETOOBIG); time-dependent terms are not taken (QTL_EINVAL).
+ * Integration as qtl_ssesolve (Euler-Maruyama with the fixed step
+ * opts->dt_fixed, FP64, the same Wiener increments), without
+ * renormalisation (the scheme keeps Tr rho = 1 up to rounding).
+ *   expect_out[n_e*nt]: trajectory mean of Tr(O_k rho);
+ *   meas_out[n_sc*nt]:  trajectory mean of J_n, recorded as in qtl_ssesolve. */
+qtl_status qtl_smesolve(qtl_system* sys, int32_t n_sc, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                        int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
+                        double* meas_out, qtl_stats* stats);
+
 /* Reusable batch plan (Sec. 3.2 over nb independent systems, as
  * qtl_mesolve_batch_async), built once and replayed.
  *   qtl_batch_create: the same arguments as qtl_mesolve_batch_async (device

@@ -231,6 +231,7 @@ struct McJob {
     const double* odiag;  // [n_e][n]: every observable real and diagonal (else null)
     double2* traj_meas;   // ssesolve: [(n*nt + t)*ntraj + j] homodyne currents (re; im = 0)
     double2* meas;        // ssesolve: [n_c*nt] their trajectory means
+    const double2* ew;    // smesolve: [n*n][n_e] trace weights, Tr(O rho) = sum_r ew[r] vec(rho)[r]
     int n_td;             // time-dependent terms f_k(t) (-i H_k), trajectory kernel n <= 1024
     const int4* tseg;     // -i H_k stacked row-wise (rows k*n + r), segmented
     const int32_t* tci;
@@ -284,6 +285,7 @@ cudaError_t launch_me_cluster(const MeJob* jobs_dev, int njobs, int L_max, int s
 cudaError_t launch_mc_traj(const McJob& job, int precision, cudaStream_t st);
 cudaError_t launch_mc_reduce(const McJob& job, cudaStream_t st);
 cudaError_t launch_sse_traj(const McJob& job, cudaStream_t st);   // ssesolve (FP64, n <= 1024)
+cudaError_t launch_sme_traj(const McJob& job, cudaStream_t st);   // smesolve (FP64, n*n <= 4096)
 // means over trajectories of traj[(row)*ntraj + j] into out[row] (fixed order)
 cudaError_t launch_traj_mean(const double2* traj, double2* out, int nrows, int ntraj, cudaStream_t st);
 constexpr int SSE_MAXSC = 4;      // stochastic operators per ssesolve

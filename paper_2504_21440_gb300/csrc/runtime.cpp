@@ -1137,6 +1137,84 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
     return QTL_OK;
 }
 
+qtl_status qtl_smesolve(qtl_system* sys, int32_t n_sc, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                        int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out, double* meas_out,
+                        qtl_stats* stats) {
+    if (!sys || !psi0 || !tlist || nt < 1 || ntraj < 1 || !meas_out) return QTL_EINVAL;
+    qtl_status st = check_opts(opts);
+    if (st != QTL_OK) return st;
+    if (!opts->fixed_step || opts->precision != QTL_FP64) return QTL_EINVAL;
+    System& s = sys->s;
+    if (n_sc < 1 || n_sc > SSE_MAXSC || n_sc > s.n_c || !s.Htd.empty()) return QTL_EINVAL;
+    if (s.n_e > 0 && !expect_out) return QTL_EINVAL;
+    if ((int64_t)s.n * s.n > 4096) return QTL_ETOOBIG;
+    if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    for (int i = 0; i < s.n; ++i)
+        if (!finite_c(psi0[i])) return QTL_EINVAL;
+    s.solved = true;
+    if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+    const size_t n = (size_t)s.n, ne = (size_t)s.n_e * nt, nm = (size_t)n_sc * nt;
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        const size_t o = off;
+        off = (off + b + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_psi = take(n * 16), o_tl = take((size_t)nt * 8), o_te = take(ne * ntraj * 16),
+                 o_tm = take(nm * ntraj * 16), o_ex = take(ne * 16), o_ms = take(nm * 16),
+                 o_inf = take(sizeof(qtl_device_info));
+    cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
+    char* buf = nullptr;
+    QTL_CUDA(qtl_malloc_async((void**)&buf, off, stream));
+    McJob J;
+    std::memset(&J, 0, sizeof(J));
+    J.n = s.n;
+    J.aseg = s.dL.seg;   // the Liouvillian of H and of every collapse operator
+    J.aci = s.dL.ci;
+    J.av64 = s.dL.v64;
+    J.n_c = n_sc;        // the measured operators: the last n_sc collapse operators
+    J.crp = s.dC.rp + (size_t)(s.n_c - n_sc) * s.n;
+    J.cci = s.dC.ci;
+    J.cv = s.dC.v64;
+    J.n_e = s.n_e;
+    J.ew = s.ew;
+    J.tlist = (const double*)(buf + o_tl);
+    J.nt = nt;
+    J.psi0 = (const double2*)(buf + o_psi);
+    J.ntraj = ntraj;
+    J.seed = seed;
+    J.traj_expect = (double2*)(buf + o_te);
+    J.expect = (double2*)(buf + o_ex);
+    J.traj_meas = (double2*)(buf + o_tm);
+    J.meas = (double2*)(buf + o_ms);
+    J.info = (qtl_device_info*)(buf + o_inf);
+    J.dt_fixed = opts->dt_fixed;
+    cudaError_t e;
+    std::vector<qtl_c128> mh(nm);
+    qtl_device_info info;
+    std::memset(&info, 0, sizeof(info));
+    if ((e = cudaMemcpyAsync(buf + o_psi, psi0, n * 16, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(buf + o_tl, tlist, (size_t)nt * 8, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(buf + o_inf, 0, sizeof(qtl_device_info), stream)) != cudaSuccess ||
+        (e = launch_sme_traj(J, stream)) != cudaSuccess ||
+        (ne > 0 && (e = cudaMemcpyAsync(expect_out, buf + o_ex, ne * 16, cudaMemcpyDeviceToHost, stream)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync(mh.data(), buf + o_ms, nm * 16, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&info, buf + o_inf, sizeof(info), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) {
+        set_cuda_error(e);
+        cudaFreeAsync(buf, stream);
+        cudaStreamSynchronize(stream);
+        return QTL_ECUDA;
+    }
+    cudaFreeAsync(buf, stream);
+    QTL_CUDA(cudaStreamSynchronize(stream));
+    for (size_t i = 0; i < nm; ++i) meas_out[i] = mh[i].re;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->steps_acc = info.steps_acc;
+    }
+    return QTL_OK;
+}
+
 int32_t qtl_system_dim(const qtl_system* sys) { return sys ? sys->s.n : 0; }
 
 int64_t qtl_system_liouvillian_nnz(const qtl_system* sys) { return sys ? sys->s.dL.nnz : 0; }

@@ -113,6 +113,9 @@ def load():
     lib.qtl_ssesolve.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(Opts), P, P,
                                  C.POINTER(Stats)]
     lib.qtl_ssesolve.restype = C.c_int
+    lib.qtl_smesolve.argtypes = [P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(Opts), P, P,
+                                 C.POINTER(Stats)]
+    lib.qtl_smesolve.restype = C.c_int
     lib.qtl_batch_create.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P, C.c_int32,
                                      C.POINTER(P)]
     lib.qtl_batch_create.restype = C.c_int
@@ -272,6 +275,21 @@ def ssesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts):
     st = Stats()
     _check(lib.qtl_ssesolve(sys, _ptr(p0), _ptr(tl), len(tl), int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
                             C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st)), "qtl_ssesolve")
+    return dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict())
+
+
+def smesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts):
+    """qtl_smesolve with host arrays (the system's last n_sc collapse operators
+    are measured).  Returns dict(expect[n_e, nt], measurement[n_sc, nt], stats)."""
+    lib = load()
+    p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    ex = np.zeros((max(n_e, 1), len(tl)), dtype=np.complex128)
+    ms = np.zeros((max(n_sc, 1), len(tl)), dtype=np.float64)
+    st = Stats()
+    _check(lib.qtl_smesolve(sys, int(n_sc), _ptr(p0), _ptr(tl), len(tl), int(ntraj),
+                            C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st)),
+           "qtl_smesolve")
     return dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict())
 
 
@@ -537,6 +555,10 @@ class System:
     def ssesolve(self, psi0, tlist, ntraj, seed, **kw):
         """The collapse operators given at construction are the stochastic operators."""
         return ssesolve(self.handle, self.n_e, self.n_c, psi0, tlist, ntraj, seed, make_opts(**kw))
+
+    def smesolve(self, n_sc, psi0, tlist, ntraj, seed, **kw):
+        """The last n_sc collapse operators given at construction are measured."""
+        return smesolve(self.handle, self.n_e, n_sc, psi0, tlist, ntraj, seed, make_opts(**kw))
 
     def sesolve(self, psi0, tlist, **kw):
         return sesolve(self.handle, self.n_e, psi0, tlist, make_opts(**kw))
