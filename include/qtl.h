@@ -11,9 +11,14 @@
  *     below a uniform threshold, channel k drawn with weight |C_k psi|^2),
  * with an adaptive embedded Runge-Kutta 5(4) pair (Dormand-Prince 1980 or
  * Tsitouras 2011) and a PI step-size controller.  The paper leaves the
- * integrator to DifferentialEquations.jl (Sec. 2); the readings fixed here
- * (error norm, controller constants, exact landing on tlist) are listed in
- * the design notes and implemented identically by the test oracle.
+ * integrator to DifferentialEquations.jl (Sec. 2); the readings fixed here,
+ * implemented identically by the test oracle, are: the error norm
+ * sqrt(mean_i |e_i|^2 / sc_i^2) over complex entries with
+ * sc_i = atol + rtol max(|y_i|, |y_new,i|); a PI controller with factor
+ * clamp(0.9 err^-0.14 err_prev^0.08, 0.2, 10) on accept (at most 1 right after
+ * a reject, err_prev floored at 1e-4) and max(0.2, 0.9 err^-0.2) on reject;
+ * the Hairer-Norsett-Wanner starting step; steps clamped to land exactly on
+ * each time of tlist.
  *
  * Conventions for every entry point:
  *   - complex numbers are interleaved {re, im} FP64 (qtl_c128);

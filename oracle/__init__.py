@@ -12,8 +12,8 @@ step after the paper:
                plain matrix product; the effective Hamiltonian (Sec. 3.3)
   tableau.py   Dormand-Prince 5(4) and Tsitouras 5(4) coefficients
   integrate.py embedded RK step, error norm, PI controller, starting step,
-               tlist landing (the paper names no integrator; see the readings
-               listed in the design notes)
+               tlist landing (the paper names no integrator; integrate.py
+               states each reading it uses)
   mesolve.py   mesolve with expectation values Tr(O rho) (Sec. 3.2)
   philox.py    Philox4x32-10 counter-based generator (Salmon et al. 2011)
   mcsolve.py   Monte-Carlo wave-function method (Sec. 3.3)

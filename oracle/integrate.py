@@ -4,7 +4,7 @@ number of output times, Sec. 3.1).
 
 The paper is silent on the method, the error norm, the step-size controller,
 the starting step and how output times are met.  The readings used (the same
-ones the CUDA library implements, each stated in the design notes):
+ones the CUDA library implements):
   * a 7-stage FSAL 5(4) pair (tableau.py);
   * error norm: RMS over complex entries of |e_i| / sc_i with
     e = h sum_j e_j k_j and sc_i = atol + rtol max(|y_i|, |y_new,i|);
