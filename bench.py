@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="jc_40x2",
-                    choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc", "optomech_td", "ssesolve_jc"])
+                    choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc", "optomech_td", "ssesolve_jc", "smesolve_jc"])
     ap.add_argument("--rates", default="10,30,100,300")
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -822,8 +822,74 @@ def run_ssesolve(args):
         "gpu_launches": launches, "clocks": clk}))
 
 
+def run_smesolve(args):
+    """Homodyne stochastic master equation (Sec. 3.4, the paper's example):
+    the JC system of the ssesolve workload (N = 20, wc = wq = 5, g = 0.1,
+    psi0 = |alpha = 2, e>) with qubit decay sqrt(gamma) sm (gamma = 2) and
+    cavity dephasing sqrt(kappa_phi) a^dag a (kappa_phi = 0.3) unmeasured,
+    homodyne detection of sqrt(kappa) a (kappa = 1), e_ops {X}, tlist =
+    range(0, 10 pi / wc, 400), 500 trajectories, Euler-Maruyama dt = 1e-3,
+    FP64.  Value: trajectories per second; the oracle is timed on 1
+    trajectory."""
+    import math
+    import scipy.sparse as sp
+    import torch
+    from paper_2504_21440_gb300 import qtl
+    from oracle.stochastic import smesolve as o_sme
+    torch.cuda.set_device(0)
+    qtl.load()
+    N, wc, wq, gc, kap, gam, kphi, alpha, ntraj = 20, 5.0, 5.0, 0.1, 1.0, 2.0, 0.3, 2.0, 500
+
+    def destroy(M):
+        return sp.diags(np.sqrt(np.arange(1, M)), 1, format="csr", dtype=complex)
+    a = sp.kron(destroy(N), sp.identity(2), format="csr")
+    sm = sp.kron(sp.identity(N), sp.csr_matrix(np.array([[0, 0], [1, 0]], dtype=complex)), format="csr")
+    sz = sp.kron(sp.identity(N), sp.csr_matrix(np.diag([1.0, -1.0]).astype(complex)), format="csr")
+    H = (wc * a.conj().T @ a + wq * sz / 2 + gc * (a.conj().T @ sm + a @ sm.conj().T)).tocsr()
+    C = [math.sqrt(gam) * sm, (math.sqrt(kphi) * a.conj().T @ a).tocsr()]
+    S = math.sqrt(kap) * a
+    X = (S + S.conj().T).tocsr()
+    k = np.arange(N)
+    coh = np.exp(-alpha ** 2 / 2) * alpha ** k / np.sqrt([math.factorial(int(q)) for q in k])
+    psi0 = np.kron(coh / np.linalg.norm(coh), np.array([1.0, 0.0]))
+    tl = np.linspace(0, 10 * math.pi / wc, 400)
+    g = qtl.System(H, C + [S], [X])
+    o = qtl.make_opts(fixed_dt=1e-3)
+    for _ in range(args.warmup):
+        qtl.smesolve(g.handle, 1, 1, psi0, tl, ntraj, 1, o)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = qtl.launch_count()
+    ms = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = qtl.smesolve(g.handle, 1, 1, psi0, tl, ntraj, 1, o)
+        ms.append(1e3 * (time.perf_counter() - t0))
+    clk = clocks.stop()
+    launches = qtl.launch_count() - l0
+    g.free()
+    mean_ms = statistics.mean(ms)
+    t0 = time.perf_counter()
+    o_sme(H, C, [S], [X], psi0, tl, 1e-3, 1, 1)
+    t_cpu = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": "smesolve traj/s (homodyne JC with losses, Sec. 3.4, 500 trajectories)",
+        "value": ntraj / (mean_ms / 1e3), "unit": "traj/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "smesolve_jc: N=20 x 2, wc=wq=5, g=0.1, C={sqrt(2) sm, sqrt(0.3) a'a}, S=a, alpha=2, t in [0, 2 pi], 400 saveat, dt 1e-3",
+                   "timing": "host API call, host buffers, copies included"},
+        "steps_per_traj": r["stats"]["steps_acc"] / ntraj, "X_final": float(r["expect"][0, -1].real),
+        "cpu_baseline": {"value": 1 / t_cpu, "unit": "traj/s", "cores": 1, "kind": "oracle",
+                         "sample": "oracle smesolve of 1 trajectory (%.1f s)" % t_cpu},
+        "gpu_launches": launches, "clocks": clk}))
+
+
 def main():
     args = parse()
+    if args.workload == "smesolve_jc" and args.impl != "reference":
+        run_smesolve(args)
+        return
     if args.workload == "ssesolve_jc" and args.impl != "reference":
         run_ssesolve(args)
         return
