@@ -19,8 +19,10 @@ step after the paper:
   mcsolve.py   Monte-Carlo wave-function method (Sec. 3.3)
   timedep.py   time-dependent Hamiltonians H0 + sum_k f_k(t) H_k (Sec. 2,
                Sec. 3.2) for mesolve and mcsolve; sesolve (Sec. 3.1)
-  stochastic.py  the stochastic Schroedinger equation under homodyne
-               detection (Sec. 3.4), Euler-Maruyama with renormalisation
+  stochastic.py  the stochastic Schroedinger and master equations under
+               homodyne detection (Sec. 3.4), Euler-Maruyama
+  steadystate.py stationary states: direct solve with the trace condition
+               (Sec. 3.2) and the Fourier-component system of Appendix A
 
 Parity status: every function here is pinned by tests/test_oracle_*.py to
 closed forms, brute-force matrix exponentials, invariants, order conditions

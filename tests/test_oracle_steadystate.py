@@ -1,0 +1,73 @@
+"""Pins of the stationary-state oracle (oracle/steadystate.py): the driven
+damped cavity's coherent steady state and the paper's photon number
+F^2 / (D^2 + k^2/4) (Sec. 5), the thermal occupation, the residual and
+invariants, long-time mesolve, and the Fourier components of a cos-driven
+cavity against its exact periodic solution (Appendix A)."""
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from oracle.lindblad import liouvillian, vec
+from oracle.mesolve import mesolve
+from oracle.steadystate import steadystate, steadystate_fourier
+
+
+def destroy(N):
+    return sp.diags(np.sqrt(np.arange(1, N)), 1, format="csr", dtype=complex)
+
+
+def test_driven_cavity_steady_state_closed_form():
+    N, D, F, kap = 40, 1.0, 0.5, 0.2
+    a = destroy(N)
+    ad = a.conj().T
+    H = D * (ad @ a) + F * (a + ad)
+    rho = steadystate(H, [math.sqrt(kap) * a])
+    ass = -1j * F / (kap / 2 + 1j * D)
+    assert abs(np.trace(a @ rho) - ass) <= 1e-12
+    assert abs(np.trace(ad @ a @ rho) - F ** 2 / (D ** 2 + kap ** 2 / 4)) <= 1e-12
+    assert abs(np.trace(rho) - 1) <= 1e-13
+    assert np.max(np.abs(rho - rho.conj().T)) <= 1e-13
+    assert np.min(np.linalg.eigvalsh((rho + rho.conj().T) / 2)) >= -1e-12
+    assert np.max(np.abs(liouvillian(H, [math.sqrt(kap) * a]) @ vec(rho))) <= 1e-12
+
+
+def test_thermal_occupation_and_long_time_mesolve():
+    N, w, kap, nth = 40, 1.0, 0.3, 0.4
+    a = destroy(N)
+    ad = a.conj().T
+    H = w * (ad @ a)
+    c = [math.sqrt(kap * (1 + nth)) * a, math.sqrt(kap * nth) * ad]
+    rho = steadystate(H, c)
+    assert abs(np.trace(ad @ a @ rho) - nth) <= 1e-9      # thermal tail beyond N = 40 only
+    r = mesolve(H, c, [ad @ a], np.eye(N)[0], [0.0, 120.0], rtol=1e-10, atol=1e-12)
+    assert abs(r["expect"][0, -1] - np.trace(ad @ a @ rho)) <= 1e-8
+
+
+def test_fourier_components_of_a_cos_driven_cavity():
+    """H = D a'a + F cos(w t)(a + a'), loss sqrt(k) a: the periodic steady
+    state is coherent with alpha(t) = A+ e^{i w t} + A- e^{-i w t},
+    A+- = -i (F/2) / (z +- i w), z = i D + k/2, so <a> has only the n = +-1
+    components and the period-averaged photon number is |A+|^2 + |A-|^2."""
+    N, D, kap, F, w = 30, 0.7, 0.5, 0.2, 1.1
+    a = destroy(N)
+    ad = a.conj().T
+    comps = steadystate_fourier(D * (ad @ a), [math.sqrt(kap) * a], a + ad, F, w, 4)
+    z = 1j * D + kap / 2
+    Ap, Am = -0.5j * F / (z + 1j * w), -0.5j * F / (z - 1j * w)
+    assert abs(np.trace(a @ comps[1]) - Ap) <= 1e-10
+    assert abs(np.trace(a @ comps[-1]) - Am) <= 1e-10
+    assert abs(np.trace(a @ comps[0])) <= 1e-10
+    assert abs(np.trace(ad @ a @ comps[0]) - (abs(Ap) ** 2 + abs(Am) ** 2)) <= 1e-10
+    assert abs(np.trace(comps[0]) - 1) <= 1e-12
+
+
+def test_fourier_without_drive_is_the_steady_state():
+    N, D, kap = 12, 0.9, 0.4
+    a = destroy(N)
+    ad = a.conj().T
+    H = D * (ad @ a) + 0.3 * (a + ad)
+    c = [math.sqrt(kap) * a]
+    comps = steadystate_fourier(H, c, a + ad, 0.0, 1.3, 2)
+    assert np.max(np.abs(comps[0] - steadystate(H, c))) <= 1e-12
+    assert all(np.max(np.abs(comps[k])) <= 1e-12 for k in (-2, -1, 1, 2))
