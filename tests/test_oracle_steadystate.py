@@ -71,3 +71,32 @@ def test_fourier_without_drive_is_the_steady_state():
     comps = steadystate_fourier(H, c, a + ad, 0.0, 1.3, 2)
     assert np.max(np.abs(comps[0] - steadystate(H, c))) <= 1e-12
     assert all(np.max(np.abs(comps[k])) <= 1e-12 for k in (-2, -1, 1, 2))
+
+
+def test_fourier_components_match_the_long_time_periodic_solution():
+    """A nonlinear case with no closed form: a Kerr cavity under F cos(w t)(a + a').
+    After the transient has decayed, rho(t) is periodic, and its Fourier
+    coefficients avg_t rho(t) e^{-i n w t} over one period (the trapezoid sum
+    on M equispaced points is exact for harmonics below M) must equal the
+    rho_n of the linear system.  The time-dependent mesolve oracle is pinned
+    separately, so this checks the block structure, the -i n w shift and the
+    trace row."""
+    from oracle.timedep import Coef, mesolve_td
+    N, D, K, kap, F, w = 10, 0.4, 0.3, 0.8, 0.35, 1.3
+    a = destroy(N)
+    ad = a.conj().T
+    H0 = (D * (ad @ a) + K * (ad @ ad @ a @ a)).tocsr()
+    X = (a + ad).tocsr()
+    c = [math.sqrt(kap) * a]
+    comps = steadystate_fourier(H0, c, X, F, w, 10)
+    P, M = 2 * math.pi / w, 32
+    T = 16.0 * P                              # e^{-kap T / 2} < 1e-13
+    tl = [0.0] + [T + j * P / M for j in range(M)]
+    r = mesolve_td(H0, [(X, Coef("cos", F, w))], c, [], np.eye(N)[0], tl,
+                   rtol=1e-11, atol=1e-13, save_states=True)
+    rhos = [np.asarray(s).reshape((N, N), order="F") if np.ndim(s) == 1 else np.asarray(s)
+            for s in r["states"][1:]]
+    for k in (-2, -1, 0, 1, 2):
+        avg = sum(rho * np.exp(-1j * k * w * t) for rho, t in zip(rhos, tl[1:])) / M
+        assert np.max(np.abs(avg - comps[k])) <= 1e-8, k
+    assert np.max(np.abs(comps[1] - comps[-1].conj().T)) <= 1e-13   # rho(t) Hermitian
