@@ -267,7 +267,8 @@ qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlis
  *   meas_out[n_c*nt]:   trajectory mean of J_n of the last step ending at or
  *                       before each time (e_n(psi0) at tlist[0]).
  * Host pointers; returns when done; stats->steps_acc = steps over all
- * trajectories. */
+ * trajectories.  QTL_ESTEP, before any work, when (tlist[nt-1] - tlist[0]) /
+ * dt_fixed exceeds opts->max_steps (a trajectory's step count). */
 qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
                         int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
                         double* meas_out, qtl_stats* stats);
@@ -282,7 +283,7 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
  * others the unmeasured C_i.  rho0 = |psi0><psi0|; n*n <= 4096
  * (QTL_ETOOBIG); time-dependent terms are not taken (QTL_EINVAL).
  * Integration as qtl_ssesolve (Euler-Maruyama with the fixed step
- * opts->dt_fixed, FP64, the same Wiener increments), without
+ * opts->dt_fixed, FP64, the same Wiener increments and step budget), without
  * renormalisation (the scheme keeps Tr rho = 1 up to rounding).
  *   expect_out[n_e*nt]: trajectory mean of Tr(O_k rho);
  *   meas_out[n_sc*nt]:  trajectory mean of J_n, recorded as in qtl_ssesolve. */

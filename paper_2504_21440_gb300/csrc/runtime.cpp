@@ -711,6 +711,15 @@ static qtl_status check_tlist_host(const double* tl, int nt) {
     return QTL_OK;
 }
 
+// Fixed-step solvers: a trajectory takes about span / dt steps (plus at most
+// one short landing step per output time); more than max_steps is refused on
+// the host, since those kernels have no step budget of their own.
+static qtl_status check_fixed_steps(const double* tl, int nt, const qtl_opts* o) {
+    const double steps = (tl[nt - 1] - tl[0]) / o->dt_fixed;
+    if (!(steps <= (double)o->max_steps)) return QTL_ESTEP;
+    return QTL_OK;
+}
+
 int64_t cta_nnz_max_of(const System& s, int C) {
     const int L = s.n * s.n;
     std::vector<int64_t> per(C, 0);
@@ -1070,6 +1079,7 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
     if (s.n_e > 0 && !expect_out) return QTL_EINVAL;
     if (s.n > 1024) return QTL_ETOOBIG;
     if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    if ((st = check_fixed_steps(tlist, nt, opts)) != QTL_OK) return st;
     for (int i = 0; i < s.n; ++i)
         if (!finite_c(psi0[i])) return QTL_EINVAL;
     s.solved = true;
@@ -1149,6 +1159,7 @@ qtl_status qtl_smesolve(qtl_system* sys, int32_t n_sc, const qtl_c128* psi0, con
     if (s.n_e > 0 && !expect_out) return QTL_EINVAL;
     if ((int64_t)s.n * s.n > 4096) return QTL_ETOOBIG;
     if ((st = check_tlist_host(tlist, nt)) != QTL_OK) return st;
+    if ((st = check_fixed_steps(tlist, nt, opts)) != QTL_OK) return st;
     for (int i = 0; i < s.n; ++i)
         if (!finite_c(psi0[i])) return QTL_EINVAL;
     s.solved = true;

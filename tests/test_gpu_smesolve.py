@@ -80,6 +80,11 @@ def test_smesolve_refuses_bad_arguments():
         g.smesolve(1, psi0, tl, 2, 1)                       # adaptive: no fixed step
     with pytest.raises(qtl.QtlError) as e2:
         g.smesolve(3, psi0, tl, 2, 1, fixed_dt=0.01)        # more measured than collapse operators
+    with pytest.raises(qtl.QtlError) as e4:
+        g.smesolve(1, psi0, tl, 2, 1, fixed_dt=0.01, max_steps=50)   # 100 steps needed
+    assert e4.value.status == qtl.QTL_ESTEP
+    r = g.smesolve(1, psi0, tl, 2, 1, fixed_dt=0.01, max_steps=100)  # the system is still usable
+    assert np.all(np.isfinite(r["expect"]))
     g.free()
     H2, C2, S2, e2_ops, p2 = _jc(40)                        # n = 80: n*n > 4096
     g2 = qtl.System(H2, C2 + S2, e2_ops)

@@ -81,6 +81,9 @@ def test_ssesolve_refuses_bad_arguments():
         g.ssesolve(psi0, tl, 2, 1)                                   # adaptive: no fixed step
     with pytest.raises(qtl.QtlError) as e2:
         g.ssesolve(psi0, tl, 2, 1, fixed_dt=0.01, precision="mixed")
+    with pytest.raises(qtl.QtlError) as e4:
+        g.ssesolve(psi0, tl, 2, 1, fixed_dt=0.01, max_steps=50)     # 100 steps needed
+    assert e4.value.status == qtl.QTL_ESTEP
     g.free()
     g2 = qtl.System(H, [], e_ops)
     with pytest.raises(qtl.QtlError) as e3:
