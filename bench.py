@@ -885,8 +885,18 @@ def run_smesolve(args):
         "gpu_launches": launches, "clocks": clk}))
 
 
+# workloads that shard over torchrun ranks; the others run on one GPU
+SHARDED = ("jc_40x2", "kerr_sweep_1024")
+
+
 def main():
     args = parse()
+    if args.impl == "reference" and args.workload != "jc_40x2":
+        # the other workloads time the oracle in their own cpu_baseline entry
+        sys.exit("bench.py: --impl reference times the jc_40x2 job; the line of --workload %s "
+                 "carries its own oracle timing (cpu_baseline)" % args.workload)
+    if args.workload not in SHARDED and int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        sys.exit("bench.py: --workload %s runs on one GPU (no torchrun)" % args.workload)
     if args.workload == "smesolve_jc" and args.impl != "reference":
         run_smesolve(args)
         return
