@@ -680,7 +680,7 @@ def serving_vs_fp64(qtl, opts_mixed, n_req=40):
 
 
 def optomech_system():
-    """The driven optomechanical system of Sec. 3.2 with the paper's
+    """The driven optomechanical system of Sec. 3.4 with the paper's
     parameters: Nc = 10, Nm = 7, wc = 1, wm = 2, g = 0.05, kappa = gamma = 0.01,
     drive F cos(w_d t)(a + a^dag) with F = 10 kappa and w_d = wc, from the
     vacuum, tlist = range(0, 5/kappa, 5000), e_ops {a^dag a}."""
@@ -702,7 +702,7 @@ def optomech_system():
 
 
 def run_optomech(args):
-    """Time-dependent mesolve: the driven optomechanical system of Sec. 3.2
+    """Time-dependent mesolve: the driven optomechanical system of Sec. 3.4
     (dimension 70) over t in [0, 500] with 5000 output times, FP64, Tsit5,
     rtol 1e-8, atol 1e-10, on the grid kernel (the path for time-dependent
     Hamiltonians).  Value: Lindblad RHS evaluations per second; the oracle
@@ -750,7 +750,7 @@ def run_optomech(args):
     t_cpu = time.perf_counter() - t0
     g.free()
     print(json.dumps({
-        "metric": "Lindblad RHS evals/s (time-dependent mesolve, driven optomechanics of Sec. 3.2)",
+        "metric": "Lindblad RHS evals/s (time-dependent mesolve, driven optomechanics of Sec. 3.4)",
         "value": int(inf[3]) / (mean_ms / 1e3), "unit": "RHS evals/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -765,7 +765,7 @@ def run_optomech(args):
 
 
 def run_ssesolve(args):
-    """Homodyne detection (Sec. 3.4, the paper's example): Jaynes-Cummings
+    """Homodyne detection (Sec. 3.5, the paper's example): Jaynes-Cummings
     with N = 20, wc = wq = 5, g = 0.1, S = sqrt(kappa) a (kappa = 1), e_ops
     {X = S + S^dag}, psi0 = |alpha = 2, e>, tlist = range(0, 10 pi / wc, 400),
     500 trajectories, Euler-Maruyama with dt = 1e-3, FP64.  Value:
@@ -811,7 +811,7 @@ def run_ssesolve(args):
     ref = o_sse(H, [S], [X], psi0, tl, 1e-3, 2, 1)
     t_cpu = time.perf_counter() - t0
     print(json.dumps({
-        "metric": "ssesolve traj/s (homodyne JC of Sec. 3.4, 500 trajectories)", "value": ntraj / (mean_ms / 1e3),
+        "metric": "ssesolve traj/s (homodyne JC of Sec. 3.5, 500 trajectories)", "value": ntraj / (mean_ms / 1e3),
         "unit": "traj/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "ssesolve_jc: N=20 x 2, wc=wq=5, g=0.1, S=sqrt(1) a, alpha=2, t in [0, 2 pi], 400 saveat, dt 1e-3",
@@ -823,7 +823,7 @@ def run_ssesolve(args):
 
 
 def run_smesolve(args):
-    """Homodyne stochastic master equation (Sec. 3.4, the paper's example):
+    """Homodyne stochastic master equation (Sec. 3.5, the paper's example):
     the JC system of the ssesolve workload (N = 20, wc = wq = 5, g = 0.1,
     psi0 = |alpha = 2, e>) with qubit decay sqrt(gamma) sm (gamma = 2) and
     cavity dephasing sqrt(kappa_phi) a^dag a (kappa_phi = 0.3) unmeasured,
@@ -873,7 +873,7 @@ def run_smesolve(args):
     o_sme(H, C, [S], [X], psi0, tl, 1e-3, 1, 1)
     t_cpu = time.perf_counter() - t0
     print(json.dumps({
-        "metric": "smesolve traj/s (homodyne JC with losses, Sec. 3.4, 500 trajectories)",
+        "metric": "smesolve traj/s (homodyne JC with losses, Sec. 3.5, 500 trajectories)",
         "value": ntraj / (mean_ms / 1e3), "unit": "traj/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",

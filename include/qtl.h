@@ -156,7 +156,7 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c,
                              const qtl_op* e_ops, int32_t n_e, qtl_system** out);
 
 /* Time-dependent Hamiltonians (Sec. 2, QobjEvo: H(t) = H0 + sum_k f_k(t) H_k;
- * the drive F cos(w_d t)(a + a^dag) of Sec. 3.2; the complex pair
+ * the drive F cos(w_d t)(a + a^dag) of Sec. 3.4; the complex pair
  * A e^{i w t} a + conj(.) a^dag of Sec. 5).  A coefficient is
  *   f(t) = (amp_re + i amp_im) * env(t) * g(omega t + phi),
  *   g = cos for QTL_COEF_COS, exp(i .) for QTL_COEF_EXP,
@@ -251,7 +251,7 @@ qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb, const qtl_c
 qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
                        const qtl_opts* opts, qtl_c128* expect_out, qtl_stats* stats);
 
-/* ssesolve (Sec. 3.4): the stochastic Schroedinger equation under homodyne
+/* ssesolve (Sec. 3.5): the stochastic Schroedinger equation under homodyne
  * detection, in Ito form d psi = -i K psi dt + sum_n M_n psi dW_n with
  * K = H + i sum_n (e_n/2 S_n - 1/2 S_n^dag S_n - e_n^2/8), M_n = S_n - e_n/2,
  * e_n = <psi|S_n + S_n^dag|psi>; the homodyne current is J_n = e_n + dW_n/dt.
@@ -273,7 +273,7 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
                         int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
                         double* meas_out, qtl_stats* stats);
 
-/* smesolve (Sec. 3.4): the stochastic master equation under homodyne
+/* smesolve (Sec. 3.5): the stochastic master equation under homodyne
  * detection, in Ito form
  *   d rho = -i[H, rho] dt + sum_i D[C_i] rho dt + sum_n D[S_n] rho dt
  *           + sum_n H[S_n] rho dW_n,

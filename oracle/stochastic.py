@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Sec. 3.4 writes the equation in Ito form,
+Sec. 3.5 writes the equation in Ito form,
     d psi = -i K psi dt + sum_n M_n psi dW_n,
     K   = H + i sum_n ( e_n/2 S_n - 1/2 S_n^dag S_n - e_n^2/8 ),
     M_n = S_n - e_n/2,   e_n = <psi| S_n + S_n^dag |psi>,
@@ -104,7 +104,7 @@ def ssesolve(H, sc_ops, e_ops, psi0, tlist, dt, ntraj, seed, keep_trajectories=F
 
 
 def sme_trajectory(H, c_ops, sc_ops, e_ops, rho0, tlist, dt, seed, traj):
-    """One trajectory of the stochastic master equation of Sec. 3.4,
+    """One trajectory of the stochastic master equation of Sec. 3.5,
         d rho = -i[H, rho] dt + sum_i D[C_i] rho dt + sum_n D[S_n] rho dt
                 + sum_n H[S_n] rho dW_n,
         H[O] rho = O rho + rho O^dag - Tr(O rho + rho O^dag) rho,

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 Sec. 2 builds time-dependent operators as a constant part plus operators
 multiplied by scalar coefficient functions of t, H(t) = H0 + sum_k f_k(t) H_k
-(QobjEvo); Sec. 3.2 solves the master equation of a driven optomechanical
+(QobjEvo); Sec. 3.4 solves the master equation of a driven optomechanical
 system with the drive term f(t) (a + a^dag), f(t) = F cos(w_d t), and the
 automatic-differentiation example of Sec. 5 uses the complex pair
 f(t) = A exp(i w t) on a and its conjugate on a^dag.  Sec. 3.1 solves the
@@ -16,7 +16,7 @@ Coefficient functions here take the form the library accepts,
     env(t) = exp(-(t - t0)^2 / (2 sigma^2)) if sigma > 0, else 1,
 with a complex amplitude A.  The master equation keeps its form with H(t) in
 place of H: the right-hand side at time t is the time-independent one for
-the Hamiltonian H(t) (Sec. 3.2, with the dissipator of lindblad.py), and a
+the Hamiltonian H(t) (Sec. 3.4; the dissipator of lindblad.py), and a
 trajectory evolves under H_eff(t) = H(t) - (i/2) sum_k C_k^dag C_k (Sec. 3.3).
 """
 import math

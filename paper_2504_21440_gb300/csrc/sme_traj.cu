@@ -1,5 +1,5 @@
 // smesolve: the stochastic master equation under homodyne detection (paper
-// Sec. 3.4), in Ito form
+// Sec. 3.5), in Ito form
 //     d rho = L rho dt + sum_n H[S_n] rho dW_n,
 //     H[S] rho = S rho + rho S^dag - Tr(S rho + rho S^dag) rho,
 // where L is the Liouvillian of H and of every collapse operator (the

@@ -1,5 +1,5 @@
 // ssesolve: the stochastic Schroedinger equation under homodyne detection
-// (paper Sec. 3.4), in Ito form
+// (paper Sec. 3.5), in Ito form
 //     d psi = -i K psi dt + sum_n M_n psi dW_n,
 //     -i K psi = A psi + sum_n (e_n/2) S_n psi - sum_n (e_n^2/8) psi,
 //     A = -i H - 1/2 sum_n S_n^dag S_n,   M_n = S_n - e_n/2,

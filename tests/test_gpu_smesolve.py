@@ -1,4 +1,4 @@
-"""smesolve (Sec. 3.4) through the C ABI: trajectory means of Tr(O rho) and
+"""smesolve (Sec. 3.5) through the C ABI: trajectory means of Tr(O rho) and
 of the homodyne currents against the oracle (the same Euler-Maruyama steps
 and Wiener increments) at 1, 2 and 4 density-matrix entries per thread, a
 homodyne-monitored damped cavity whose trajectories stay coherent, and the

@@ -1,4 +1,4 @@
-"""ssesolve (Sec. 3.4) through the C ABI: trajectory means of the
+"""ssesolve (Sec. 3.5) through the C ABI: trajectory means of the
 expectation values and of the homodyne currents against the oracle (the
 same Euler-Maruyama steps and Wiener increments), a homodyne-monitored
 damped cavity whose trajectories keep their coherent state, and the

@@ -143,7 +143,7 @@ def test_mesolve_td_parity_and_closed_form(which, engine):
 
 @pytest.mark.parametrize("engine", ["cluster", "grid"])
 def test_paper_driven_optomechanics_short_time(engine):
-    """Sec. 3.2's driven optomechanical system (Nc = 10, Nm = 7), drive
+    """Sec. 3.4's driven optomechanical system (Nc = 10, Nm = 7), drive
     F cos(w_d t)(a + a^dag), losses on both modes, from the vacuum: FP64 grid
     mesolve at fixed steps against the oracle."""
     qtl = require_gpu()

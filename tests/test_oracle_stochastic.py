@@ -1,5 +1,5 @@
 """Pins of the stochastic Schroedinger equation oracle (oracle/stochastic.py,
-Sec. 3.4): the Box-Muller normals, the scheme's exact phase without
+Sec. 3.5): the Box-Muller normals, the scheme's exact phase without
 monitoring, a homodyne-monitored damped cavity whose coherent state every
 trajectory keeps, and the dephasing rate of the ensemble mean."""
 import math

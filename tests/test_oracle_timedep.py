@@ -88,7 +88,7 @@ def test_complex_exp_pair_drive_coherent_mesolve_and_trajectories():
 
 
 def test_cos_drive_closed_form_both_rhs_forms():
-    """The drive of Sec. 3.2, F cos(w_d t)(a + a'), on a damped cavity."""
+    """The drive of Sec. 3.4, F cos(w_d t)(a + a'), on a damped cavity."""
     N, D, kap, F, w = 16, 0.7, 0.5, 0.4, 1.1
     a = destroy(N)
     tl = np.linspace(0, 10, 21)
