@@ -23,6 +23,8 @@ step after the paper:
                homodyne detection (Sec. 3.4), Euler-Maruyama
   steadystate.py stationary states: direct solve with the trace condition
                (Sec. 3.2) and the Fourier-component system of Appendix A
+  dsf.py       the dynamical shifted Fock master equation (Sec. 3.6,
+               Appendix B, Algorithm 1)
 
 Parity status: every function here is pinned by tests/test_oracle_*.py to
 closed forms, brute-force matrix exponentials, invariants, order conditions

@@ -1,0 +1,90 @@
+"""Pins of the dynamical-shifted-Fock oracle (oracle/dsf.py; Sec. 3.6,
+Appendix B): a strongly driven damped cavity, whose exact state is the
+coherent state alpha(t) = alpha_ss (1 - e^{-(k/2 + i D) t}), followed with a
+Fock cutoff of 8 where the plain solve fails; the paper's two-mode model with
+a Kerr mode and a nonlinear coupling against a plain mesolve at a cutoff that
+holds the whole displaced state; and an unreached threshold, which reduces
+DSF to the plain solve."""
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+from oracle.dsf import dsf_mesolve
+from oracle.mesolve import mesolve
+
+
+def destroy(N):
+    return sp.diags(np.sqrt(np.arange(1, N)), 1, format="csr", dtype=complex)
+
+
+def test_driven_cavity_follows_the_coherent_state_with_a_small_cutoff():
+    N, D, F, kap = 8, 0.5, 7.0, 1.0
+    a = destroy(N)
+    tl = np.linspace(0.0, 6.0, 301)
+    H = lambda o: D * (o[0].conj().T @ o[0]) + F * (o[0] + o[0].conj().T)
+    c = lambda o: [math.sqrt(kap) * o[0]]
+    e = lambda o: [o[0], o[0].conj().T @ o[0]]
+    r = dsf_mesolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.05, rtol=1e-10, atol=1e-12)
+    ass = -1j * F / (kap / 2 + 1j * D)
+    al = ass * (1 - np.exp(-(kap / 2 + 1j * D) * tl))
+    assert abs(ass) > 9.8                                   # <n> near 98 photons
+    assert np.max(np.abs(r["expect"][0] - al)) <= 1e-6
+    assert np.max(np.abs(r["expect"][1] - np.abs(al) ** 2)) <= 1e-5
+    assert np.max(np.abs(r["alpha"][0] - al)) <= 0.06      # tracked within the threshold
+    assert r["shifts"] > 100
+    plain = mesolve(H([a]), c([a]), [a], np.eye(N)[0], tl, rtol=1e-10, atol=1e-12)
+    assert np.max(np.abs(plain["expect"][0] - al)) > 1.0    # the cutoff alone cannot hold it
+
+
+def test_two_mode_kerr_model_matches_a_large_cutoff_solve():
+    """Sec. 3.6's model: D1 a1'a1 + D2 a2'a2 - U a2'^2 a2^2 + J (a1 a2'^2 +
+    a1' a2^2) + F (a1 + a1'), losses a1, a2^2; DSF on mode 1 only.  F is
+    lowered to 1.5 so that a plain solve with mode 1 cut at 30 holds the state
+    (cut at 22 it is already within 2e-6).  DSF converges in its own cutoff:
+    5 states leave 2e-3, 7 leave 2e-5, 9 leave the reference's error."""
+    D1, D2, U, J, F, k1, k22 = 0.5, 0.5, 0.05, 0.3, 1.5, 1.0, 0.01
+    N1s, N1, N2 = 9, 30, 6
+    tl = np.linspace(0.0, 4.0, 81)
+
+    def model(N1_):
+        a1 = sp.kron(destroy(N1_), sp.identity(N2), format="csr")
+        a2 = sp.kron(sp.identity(N1_), destroy(N2), format="csr")
+        a2d = a2.conj().T
+
+        def H(o):
+            b = o[0]
+            return (D1 * (b.conj().T @ b) + D2 * (a2d @ a2) - U * (a2d @ a2d @ a2 @ a2)
+                    + J * (b @ a2d @ a2d + b.conj().T @ a2 @ a2) + F * (b + b.conj().T))
+
+        c = lambda o: [math.sqrt(k1) * o[0], math.sqrt(k22) * (a2 @ a2)]
+        e = lambda o: [o[0].conj().T @ o[0], a2d @ a2, o[0], a2]
+        return a1, H, c, e
+
+    a1, H, c, e = model(N1s)
+    psi0 = np.zeros(N1s * N2)
+    psi0[0] = 1.0
+    r = dsf_mesolve(H, c, e, [a1], [0.0], psi0, tl, 0.1, rtol=1e-10, atol=1e-12)
+    b1, Hb, cb, eb = model(N1)
+    p0 = np.zeros(N1 * N2)
+    p0[0] = 1.0
+    ref = mesolve(Hb([b1]), cb([b1]), eb([b1]), p0, tl, rtol=1e-10, atol=1e-12)
+    assert np.max(np.abs(ref["expect"][0])) > 3.0           # mode 1 well beyond the small cutoff
+    assert np.max(np.abs(ref["expect"][1])) > 1e-3          # mode 2 fed by the coupling
+    assert np.max(np.abs(r["expect"] - ref["expect"])) <= 1e-6
+    assert r["shifts"] > 10
+    small = mesolve(H([a1]), c([a1]), e([a1]), psi0, tl, rtol=1e-10, atol=1e-12)
+    assert np.max(np.abs(small["expect"] - ref["expect"])) > 1e-3   # the same cutoff without DSF
+
+
+def test_unreached_threshold_is_the_plain_solve():
+    N = 6
+    a = destroy(N)
+    tl = np.linspace(0.0, 2.0, 11)
+    H = lambda o: 0.3 * (o[0].conj().T @ o[0]) + 0.2 * (o[0] + o[0].conj().T)
+    c = lambda o: [math.sqrt(0.5) * o[0]]
+    e = lambda o: [o[0], o[0].conj().T @ o[0]]
+    r = dsf_mesolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 1e9, rtol=1e-10, atol=1e-12)
+    ref = mesolve(H([a]), c([a]), e([a]), np.eye(N)[0], tl, rtol=1e-10, atol=1e-12)
+    assert r["shifts"] == 0
+    assert np.max(np.abs(r["expect"] - ref["expect"])) <= 1e-9
