@@ -1,7 +1,8 @@
 """Pins of the stationary-state oracle (oracle/steadystate.py): the driven
 damped cavity's coherent steady state and the paper's photon number
 F^2 / (D^2 + k^2/4) (Sec. 5), the thermal occupation, the residual and
-invariants, long-time mesolve, and the Fourier components of a cos-driven
+invariants, long-time mesolve, the derivative in the drive frequency printed
+in Sec. 5, and the Fourier components of a cos-driven
 cavity against its exact periodic solution (Appendix A)."""
 import math
 
@@ -100,3 +101,22 @@ def test_fourier_components_match_the_long_time_periodic_solution():
         avg = sum(rho * np.exp(-1j * k * w * t) for rho, t in zip(rhos, tl[1:])) / M
         assert np.max(np.abs(avg - comps[k])) <= 1e-8, k
     assert np.max(np.abs(comps[1] - comps[-1].conj().T)) <= 1e-13   # rho(t) Hermitian
+
+
+def test_photon_number_derivative_in_the_drive_frequency():
+    """Sec. 5's driven oscillator in the frame rotating at w_d (D = w_c - w_d):
+    a central difference of the steady-state photon number in w_d equals the
+    printed derivative 2 F^2 D / (D^2 + g^2/4)^2, at several detunings."""
+    N, wc, F, g, h = 40, 1.0, 0.3, 0.5, 1e-4
+    a = destroy(N)
+    ad = a.conj().T
+
+    def n_ss(wd):
+        rho = steadystate((wc - wd) * (ad @ a) + F * (a + ad), [math.sqrt(g) * a])
+        return np.trace(ad @ a @ rho).real
+
+    for wd in (0.6, 0.9, 1.0, 1.2):
+        D = wc - wd
+        fd = (n_ss(wd + h) - n_ss(wd - h)) / (2 * h)
+        exact = 2 * F ** 2 * D / (D ** 2 + g ** 2 / 4) ** 2
+        assert abs(fd - exact) <= 1e-6 * max(1.0, abs(exact)), wd
