@@ -4,7 +4,8 @@ coherent state alpha(t) = alpha_ss (1 - e^{-(k/2 + i D) t}), followed with a
 Fock cutoff of 8 where the plain solve fails; the paper's two-mode model with
 a Kerr mode and a nonlinear coupling against a plain mesolve at a cutoff that
 holds the whole displaced state; and an unreached threshold, which reduces
-DSF to the plain solve."""
+DSF to the plain solve; and two displaced modes against their exact linear
+equations."""
 import math
 
 import numpy as np
@@ -88,3 +89,30 @@ def test_unreached_threshold_is_the_plain_solve():
     ref = mesolve(H([a]), c([a]), e([a]), np.eye(N)[0], tl, rtol=1e-10, atol=1e-12)
     assert r["shifts"] == 0
     assert np.max(np.abs(r["expect"] - ref["expect"])) <= 1e-9
+
+
+def test_two_displaced_modes_follow_the_linear_coherent_solution():
+    """DSF on both modes of two driven, lossy cavities with a beam-splitter
+    coupling J (a1' a2 + a1 a2'): the state stays coherent, with
+    d alpha/dt = M alpha + f, M = [[-i D1 - k1/2, -i J], [-i J, -i D2 - k2/2]],
+    f = (-i F, 0), solved exactly by the exponential of the augmented 3x3
+    system.  Each mode keeps its own tracked coherence."""
+    import scipy.linalg as sla
+    N, D1, D2, J, F, k1, k2 = 5, 0.4, -0.3, 0.8, 4.0, 1.0, 0.6
+    a1 = sp.kron(destroy(N), sp.identity(N), format="csr")
+    a2 = sp.kron(sp.identity(N), destroy(N), format="csr")
+    tl = np.linspace(0.0, 5.0, 251)
+    H = lambda o: (D1 * (o[0].conj().T @ o[0]) + D2 * (o[1].conj().T @ o[1])
+                   + J * (o[0].conj().T @ o[1] + o[0] @ o[1].conj().T) + F * (o[0] + o[0].conj().T))
+    c = lambda o: [math.sqrt(k1) * o[0], math.sqrt(k2) * o[1]]
+    e = lambda o: [o[0], o[1]]
+    psi0 = np.zeros(N * N)
+    psi0[0] = 1.0
+    r = dsf_mesolve(H, c, e, [a1, a2], [0.0, 0.0], psi0, tl, 0.03, rtol=1e-10, atol=1e-12)
+    M = np.array([[-1j * D1 - k1 / 2, -1j * J, -1j * F],
+                  [-1j * J, -1j * D2 - k2 / 2, 0.0],
+                  [0.0, 0.0, 0.0]])
+    exact = np.array([(sla.expm(M * t) @ np.array([0.0, 0.0, 1.0]))[:2] for t in tl]).T
+    assert np.min(np.max(np.abs(exact), axis=1)) > 1.5        # both modes leave the small cutoff
+    assert np.max(np.abs(r["expect"] - exact)) <= 1e-6
+    assert np.max(np.abs(r["alpha"] - exact)) <= 0.04
