@@ -3,9 +3,9 @@ Appendix B): a strongly driven damped cavity, whose exact state is the
 coherent state alpha(t) = alpha_ss (1 - e^{-(k/2 + i D) t}), followed with a
 Fock cutoff of 8 where the plain solve fails; the paper's two-mode model with
 a Kerr mode and a nonlinear coupling against a plain mesolve at a cutoff that
-holds the whole displaced state; and an unreached threshold, which reduces
-DSF to the plain solve; and two displaced modes against their exact linear
-equations."""
+holds the whole displaced state; two displaced modes against their exact
+linear equations; and an unreached threshold, which reduces DSF to the plain
+solve."""
 import math
 
 import numpy as np
