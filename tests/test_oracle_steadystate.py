@@ -1,8 +1,8 @@
 """Pins of the stationary-state oracle (oracle/steadystate.py): the driven
 damped cavity's coherent steady state and the paper's photon number
 F^2 / (D^2 + k^2/4) (Sec. 5), the thermal occupation, the residual and
-invariants, long-time mesolve, the derivative in the drive frequency printed
-in Sec. 5, and the Fourier components of a cos-driven
+invariants, long-time mesolve, a random system's SVD null space, the
+derivative in the drive frequency printed in Sec. 5, and the Fourier components of a cos-driven
 cavity against its exact periodic solution (Appendix A)."""
 import math
 
@@ -120,3 +120,22 @@ def test_photon_number_derivative_in_the_drive_frequency():
         fd = (n_ss(wd + h) - n_ss(wd - h)) / (2 * h)
         exact = 2 * F ** 2 * D / (D ** 2 + g ** 2 / 4) ** 2
         assert abs(fd - exact) <= 1e-6 * max(1.0, abs(exact)), wd
+
+
+def test_random_system_against_the_null_space():
+    """A random 5-level system with three random collapse operators: the
+    direct solve equals the null vector of the full Liouvillian (an SVD),
+    scaled to unit trace, and that null space is one-dimensional."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(7)
+    n = 5
+    M = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    H = sp.csr_matrix((M + M.conj().T) / 2)
+    cs = [sp.csr_matrix(0.5 * (rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))) for _ in range(3)]
+    rho = steadystate(H, cs)
+    L = np.asarray(liouvillian(H, cs).todense())
+    ns = sla.null_space(L, rcond=1e-10)
+    assert ns.shape[1] == 1
+    v = ns[:, 0].reshape((n, n), order="F")
+    v = v / np.trace(v)
+    assert np.max(np.abs(rho - v)) <= 1e-12
