@@ -212,7 +212,8 @@ qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket,
                        qtl_c128* expect_out, qtl_c128* states_out, qtl_stats* stats);
 
 /* Same as qtl_mesolve with device pointers, enqueued on opts->cuda_stream.
- * Scratch is taken stream-ordered from the device's default memory pool and
+ * Scratch is taken stream-ordered from a memory pool that the library owns
+ * on each device (freed blocks stay cached in it, up to 16 GiB) and
  * returned on the same stream.  Argument errors found on the host are
  * returned directly; errors found by the kernel (tlist order, step failure)
  * land in info->status. */
@@ -413,8 +414,11 @@ void qtl_server_free(qtl_server* srv);
  * allocate device memory while they solve -- code running during CUDA stream
  * capture (cudaMalloc is not allowed there), processes whose device memory is
  * owned by another allocator or a fixed budget, and latency-critical loops
- * that must not wait on the driver's allocator.  It does what
- * qtl_mcsolve_async does (same kernels, same results) but allocates nothing:
+ * that must not wait on the driver's allocator.  It runs the register-
+ * resident trajectory kernel of qtl_mcsolve_async (n <= 1024), with plain
+ * CSR rows and general observables in place of that call's segmented rows and
+ * diagonal-observable path, so the two agree to rounding (the library's tests
+ * check 1e-8 in FP64, 1e-6 in mixed precision), and it allocates nothing:
  *   - every input is a caller-owned DEVICE array: A = -i H_eff as an n x n
  *     CSR (row pointers a_row_ptr[n+1], column indices and complex values of
  *     a_nnz entries), the n_c collapse operators stacked row-wise in one CSR
@@ -427,7 +431,11 @@ void qtl_server_free(qtl_server* srv);
  *     file-scope device array of QTL_NOALLOC_SCRATCH_BYTES (32 MiB) that the
  *     library holds on every GPU that loads it until the process exits.
  * Requests whose scratch would exceed that size return QTL_ETOOBIG; n is
- * limited to 1024 (QTL_ETOOBIG above).  The first call on a device looks up
+ * limited to 1024 (QTL_ETOOBIG above).  A's structure is checked on the
+ * device (row pointers from 0 to a_nnz, non-decreasing, columns in [0, n)):
+ * a malformed A sets info->status = QTL_EINVAL and the trajectories run on
+ * empty rows.  The collapse and observable CSR arrays are not checked and
+ * must be well formed.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device
  * current; make that first call before any stream capture.  All calls share
  * the one array, which keeps the previous call's contents: calls that overlap

@@ -62,10 +62,12 @@ struct BlockReducer {
     }
     __device__ void finish(int nv) {
         __syncthreads();
-        if (tid < nv) {
+        // strided: nv may exceed the CTA's thread count (a 32-thread CTA
+        // with 64 channels, or 1 + 2 * 64 observable slots)
+        for (int i = tid; i < nv; i += blockDim.x) {
             double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += wred[w * rs + tid];
-            out[tid] = s;
+            for (int w = 0; w < nw; ++w) s += wred[w * rs + i];
+            out[i] = s;
         }
         __syncthreads();
     }

@@ -55,18 +55,38 @@ static qtl_status noalloc_scratch(void** out) {
 }
 
 // Row segments for plain CSR rows (every entry in the complex group) and,
-// for the mixed precision, the complex64 copy of A.
-__global__ void noalloc_prep_kernel(int n, const int32_t* __restrict__ rp, int4* __restrict__ seg,
+// for the mixed precision, the complex64 copy of A.  Block 0 also checks A's
+// structure (row pointers from 0 to a_nnz, non-decreasing, columns in
+// [0, n)); a malformed A sets info->status = QTL_EINVAL and gets empty row
+// segments, so the trajectory kernel that follows reads nothing outside the
+// caller's arrays.  n <= 1024, so one block holds a thread per row.
+__global__ void noalloc_prep_kernel(int n, const int32_t* __restrict__ rp,
+                                    const int32_t* __restrict__ ci, int4* __restrict__ seg,
                                     int64_t nnz, const double2* __restrict__ a64,
-                                    float2* __restrict__ a32) {
-    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = i0; r < n; r += stride) {
-        const int b = rp[r];
-        seg[r] = make_int4(b, b, b, rp[r + 1]);
+                                    float2* __restrict__ a32, qtl_device_info* info) {
+    if (blockIdx.x == 0) {
+        bool bad = false;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const int b = rp[r], e = rp[r + 1];
+            if (b < 0 || e < b || e > nnz || (r == 0 && b != 0) || (r == n - 1 && e != nnz)) {
+                bad = true;
+                continue;
+            }
+            for (int p = b; p < e; ++p)
+                if (ci[p] < 0 || ci[p] >= n) bad = true;
+        }
+        bad = __syncthreads_or(bad);
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const int b = bad ? 0 : rp[r];
+            seg[r] = make_int4(b, b, b, bad ? 0 : rp[r + 1]);
+        }
+        if (bad && threadIdx.x == 0) atomicCAS((int*)&info->status, 0, (int)QTL_EINVAL);
     }
-    if (a32)
+    if (a32) {
+        const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         for (int64_t p = i0; p < nnz; p += stride) a32[p] = make_float2((float)a64[p].x, (float)a64[p].y);
+    }
 }
 
 }  // namespace qtl
@@ -106,13 +126,12 @@ extern "C" qtl_status qtl_mcsolve_noalloc(
 
     cudaError_t e = cudaMemsetAsync(info, 0, sizeof(qtl_device_info), stream);
     if (e == cudaSuccess) {
-        const int64_t work = a32 ? (a_nnz > n ? a_nnz : n) : n;
-        int grid = (int)((work + 255) / 256);
+        int grid = a32 ? (int)((a_nnz + 1023) / 1024) : 1;
         if (grid > 1024) grid = 1024;
         if (grid < 1) grid = 1;
         count_launch();
-        noalloc_prep_kernel<<<grid, 256, 0, stream>>>(n, a_row_ptr, seg, a_nnz,
-                                                       (const double2*)a_vals, a32);
+        noalloc_prep_kernel<<<grid, 1024, 0, stream>>>(n, a_row_ptr, a_col_idx, seg, a_nnz,
+                                                        (const double2*)a_vals, a32, info);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

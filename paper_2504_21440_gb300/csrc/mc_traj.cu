@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                     red.stage(1 + e, sr);
                 }
                 red.finish(1 + J.n_e);
-                if (tid < J.n_e)
-                    J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] = make_double2(bout[1 + tid] / bout[0], 0.0);
+                for (int e = tid; e < J.n_e; e += blockDim.x)
+                    J.traj_expect[((size_t)e * J.nt + idx) * J.ntraj + jt] = make_double2(bout[1 + e] / bout[0], 0.0);
                 return bout[0];
             }
             double s2 = 0.0;
@@ -178,10 +178,10 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                 red.stage(2 + 2 * e, si);
             }
             red.finish(1 + 2 * J.n_e);
-            if (tid < J.n_e) {
+            for (int e = tid; e < J.n_e; e += blockDim.x) {
                 const double nn = bout[0];
-                J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] =
-                    make_double2(bout[1 + 2 * tid] / nn, bout[2 + 2 * tid] / nn);
+                J.traj_expect[((size_t)e * J.nt + idx) * J.ntraj + jt] =
+                    make_double2(bout[1 + 2 * e] / nn, bout[2 + 2 * e] / nn);
             }
             return bout[0];
         };

@@ -391,10 +391,10 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                 red.stage(2 + 2 * e, si);
             }
             red.finish(1 + 2 * J.n_e);
-            if (tid < J.n_e) {
+            for (int e = tid; e < J.n_e; e += blockDim.x) {
                 const double nn = bout[0];
-                J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] =
-                    make_double2(bout[1 + 2 * tid] / nn, bout[2 + 2 * tid] / nn);
+                J.traj_expect[((size_t)e * J.nt + idx) * J.ntraj + jt] =
+                    make_double2(bout[1 + 2 * e] / nn, bout[2 + 2 * e] / nn);
             }
             return bout[0];
         };

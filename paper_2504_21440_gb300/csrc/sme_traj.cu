@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(1024) sme_traj_kernel(McJob J) {
                 red.stage(2 * k + 1, si);
             }
             red.finish(2 * J.n_e);
-            if (tid < J.n_e)
-                J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] =
-                    make_double2(bout[2 * tid], bout[2 * tid + 1]);
+            for (int e = tid; e < J.n_e; e += blockDim.x)
+                J.traj_expect[((size_t)e * J.nt + idx) * J.ntraj + jt] =
+                    make_double2(bout[2 * e], bout[2 * e + 1]);
             if (tid < nsc)
                 J.traj_meas[((size_t)tid * J.nt + idx) * J.ntraj + jt] = make_double2(cb.js[tid], 0.0);
             __syncthreads();

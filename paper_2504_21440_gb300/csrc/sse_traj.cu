@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(256) sse_traj_kernel(McJob J) {
                 red.stage(2 + 2 * e, si);
             }
             red.finish(1 + 2 * J.n_e);
-            if (tid < J.n_e) {
+            for (int e = tid; e < J.n_e; e += blockDim.x) {
                 const double nn = bout[0];
-                J.traj_expect[((size_t)tid * J.nt + idx) * J.ntraj + jt] =
-                    make_double2(bout[1 + 2 * tid] / nn, bout[2 + 2 * tid] / nn);
+                J.traj_expect[((size_t)e * J.nt + idx) * J.ntraj + jt] =
+                    make_double2(bout[1 + 2 * e] / nn, bout[2 + 2 * e] / nn);
             }
             if (tid < nsc)
                 J.traj_meas[((size_t)tid * J.nt + idx) * J.ntraj + jt] = make_double2(cb.js[tid], 0.0);

@@ -135,3 +135,44 @@ def test_sharded_ranges_reproduce_the_full_ensemble():
         acc = acc + part["expect"] * count
     g.free()
     assert maxabs(acc / 101, full["expect"]) <= 1e-13
+
+
+def _random_many_channel_system(n=20, n_c=40, n_e=20, seed=12):
+    """A random n-level system with more collapse operators (n_c) and more
+    observable slots (1 + 2 n_e) than a 32-thread trajectory CTA has threads."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+
+    def herm(density):
+        m = sp.random(n, n, density=density, random_state=rng, dtype=np.float64)
+        m = m + 1j * sp.random(n, n, density=density, random_state=rng, dtype=np.float64)
+        return sp.csr_matrix((m + m.conj().T) * 0.5)
+
+    H = herm(0.2)
+    c_ops = []
+    for _ in range(n_c):
+        m = sp.random(n, n, density=0.05, random_state=rng, dtype=np.float64)
+        c_ops.append(sp.csr_matrix(m * 0.15 + 0j))
+    e_ops = [herm(0.15) for _ in range(n_e)]
+    psi0 = np.zeros(n, complex)
+    psi0[0] = 1.0
+    return H, c_ops, e_ops, psi0
+
+
+def test_many_observables_and_channels_in_a_32_thread_cta():
+    """n = 20 runs in a 32-thread CTA; 20 general observables need 41
+    reduction slots and 40 channels 40 jump weights.  Every slot must be
+    reduced and every observable saved."""
+    qtl = require_gpu()
+    H, c_ops, e_ops, psi0 = _random_many_channel_system()
+    tl = np.linspace(0.0, 6.0, 13)
+    ref = oracle_mcsolve(H, c_ops, e_ops, psi0, tl, ntraj=12, seed=31, keep_trajectories=True)
+    g = qtl.System(H, c_ops, e_ops)
+    try:
+        got = g.mcsolve(psi0, tl, 12, 31, keep_trajectories=True)
+    finally:
+        g.free()
+    assert ref["stats"]["jumps"] > 0
+    assert got["stats"]["jumps"] == ref["stats"]["jumps"]
+    assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-8
+    assert maxabs(got["expect"], ref["expect"]) <= 1e-8

@@ -73,3 +73,28 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     with pytest.raises(qtl.QtlError) as e:
         qtl.mcsolve_noalloc(2, a, c, 1, o, 2, psi, tl, 2000, 1, opts, ex, info)
     assert e.value.status == qtl.QTL_ETOOBIG
+
+
+def test_noalloc_reports_a_malformed_operator_in_its_status():
+    """A whose row pointers do not end at its entry count, or whose columns
+    leave [0, n), is refused by the device-side check with QTL_EINVAL in
+    info->status (the trajectory kernel then sees empty rows and reads
+    nothing outside the caller's arrays)."""
+    qtl = require_gpu()
+    import torch
+    dev = torch.device("cuda:0")
+    s = W.jaynes_cummings(N=4, nt=5, t_end=4.0, kappa=0.1)
+    rp, ci, v = _dev_csr((-1j * effective_hamiltonian(s.H, s.c_ops)).tocsr(), dev)
+    c = _dev_csr(sp.vstack(s.c_ops), dev)
+    o = _dev_csr(sp.vstack(s.e_ops), dev)
+    psi = torch.from_numpy(s.psi0).to(dev)
+    tl = torch.from_numpy(s.tlist).to(dev)
+    opts = qtl.make_opts(stream=torch.cuda.current_stream(dev).cuda_stream)
+    bad_col = ci.clone()
+    bad_col[-1] = s.n + 5
+    for a in [(rp, ci[:-2].clone(), v[:-2].clone()), (rp, bad_col, v)]:
+        ex = torch.zeros((len(s.e_ops), len(s.tlist)), dtype=torch.complex128, device=dev)
+        info = torch.zeros(5, dtype=torch.int64, device=dev)
+        qtl.mcsolve_noalloc(s.n, a, c, len(s.c_ops), o, len(s.e_ops), psi, tl, 4, 1, opts, ex, info)
+        torch.cuda.synchronize(dev)
+        assert int(info.cpu().numpy()[0]) & 0xffffffff == qtl.QTL_EINVAL
