@@ -73,7 +73,13 @@ def error_norm(y, y_new, ks, h, tab, rtol, atol):
 
 
 class PIController:
-    def __init__(self):
+    """beta1, beta2: the exponents of the accept factor.  The defaults are
+    the PI reading; beta2 = 0 with beta1 = 1/5 is the plain (integral)
+    controller of a 5(4) pair."""
+
+    def __init__(self, beta1=BETA1, beta2=BETA2):
+        self.beta1 = beta1
+        self.beta2 = beta2
         self.err_prev = ERR_PREV_FLOOR
         self.last_rejected = False
 
@@ -81,7 +87,7 @@ class PIController:
         if err == 0.0:
             fac = FAC_MAX
         else:
-            fac = SAFETY * err ** (-BETA1) * self.err_prev ** BETA2
+            fac = SAFETY * err ** (-self.beta1) * self.err_prev ** self.beta2
         fac = min(FAC_MAX, max(FAC_MIN, fac))
         if self.last_rejected:
             fac = min(fac, 1.0)
@@ -119,14 +125,16 @@ def initial_step(f, t0, y0, f0, rtol, atol):
 
 
 def integrate(f, y0, tlist, tab, rtol, atol, on_save, dt0=0.0, fixed_dt=None,
-              max_steps=10_000_000, dt_min=0.0, after_accept=None, stats=None):
+              max_steps=10_000_000, dt_min=0.0, after_accept=None, stats=None,
+              beta1=BETA1, beta2=BETA2):
     """Integrate y' = f(t, y) from tlist[0], calling on_save(idx, t, y) at
     every tlist point (steps land on them exactly).
 
     fixed_dt: if given, every step has size min(fixed_dt, time to the next
     tlist point) and is accepted without error control.
     after_accept(t, y, k1, h, t_new, y_new, k_last) may return a replacement
-    (t, y, k1) to restart from (used by the quantum-jump method)."""
+    (t, y, k1) to restart from (used by the quantum-jump method).
+    beta1, beta2: the step controller's exponents (PIController)."""
     st = stats if stats is not None else Stats()
     t = float(tlist[0])
     y = np.array(y0, dtype=np.complex128)
@@ -140,7 +148,7 @@ def integrate(f, y0, tlist, tab, rtol, atol, on_save, dt0=0.0, fixed_dt=None,
     else:
         h = initial_step(f, t, y, k1, rtol, atol)
         st.rhs_evals += 1
-    ctrl = PIController()
+    ctrl = PIController(beta1, beta2)
     nsteps = 0
     for idx in range(1, len(tlist)):
         t_target = float(tlist[idx])
