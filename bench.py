@@ -1,20 +1,27 @@
 #!/usr/bin/env python
 """Benchmark of the Lindblad / quantum-trajectory hot path on GB300.
 
-Workload (default `jc_40x2`): the Jaynes-Cummings cavity (x) qubit, N = 40 x 2
-(Hilbert dimension 80, Liouvillian 6400 x 6400 CSR), H = wc a'a + wq sz/2 +
-g (a s+ + a' s-) with g = 0.1, wc = wq = 1, C = sqrt(0.05) a and
-sqrt(0.02) s-, rho0 = |0> (x) |e>, tlist = range(0, 10 pi / g, 1000),
-Tsit5 with rtol 1e-8, atol 1e-10, all in FP64.  One step is one pass of the
-whole path over this job: one mesolve (Liouvillian RHS, adaptive RK 5(4),
-expectation values) and one mcsolve with 1000 trajectories (Philox stream
-seed 1), the two solves running concurrently on two CUDA streams.
+Default workload (`ising_c2`, the largest configuration that fits one GPU):
+the dissipative transverse-field Ising chain, J = 1, h ~ U[0.5, 1.5] (seed 3),
+sigma-minus loss gamma = 0.1 on every site, all spins excited, t in [0, 10]
+with 100 output times, e_ops Sx, Sy, Sz, mixed precision (FP32 right-hand
+side, FP64 state, controller and jump logic), rtol 1e-7, atol 1e-9.  One step
+is one pass of the whole path: a mesolve of 10 spins (a density matrix with
+2^20 entries, product-form RHS on the grid kernel) followed on the same
+stream by an mcsolve of 14 spins (n = 16,384) with 2000 trajectories
+(Philox seed 3).
 
-Printed (rank 0, one JSON line): Lindblad RHS evaluations per second of the
-whole job, with trajectories per second and p50/p99 job latency beside it,
-a roofline object for the dominant kernel, the FP64 oracle timed on the host
-cores (cpu_baseline), and the same metric end to end through the C ABI with
-host buffers (e2e).
+Printed (rank 0, one JSON line): Lindblad RHS evaluations of the step's
+mesolve per second of the whole step, mcsolve trajectories per second of the
+whole step, each solve's own rate and p50/p99 latency, the error of the
+reduced-precision results against FP64, a roofline object for the dominant
+kernel, the FP64 oracle timed on a bounded sample on one core and on all host
+cores (cpu_baseline), the same job end to end through the host-pointer C ABI
+(e2e), the single-solve latency of the driven cavity (N = 20) and the
+Jaynes-Cummings job (N = 40 x 2) as extra keys.
+
+Other workloads (`--workload`): jc_40x2, ising10, ising14_mc,
+kerr_sweep_1024, serving, optomech_td, ssesolve_jc, smesolve_jc.
 
 Under torchrun each rank runs the same job on its own GPU (independent
 problems, no collective on the data path): weak scaling.
@@ -52,7 +59,7 @@ def parse():
     ap.add_argument("--impl", default="qtl", choices=["qtl", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="jc_40x2",
+    ap.add_argument("--workload", default="ising_c2",
                     choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc", "optomech_td", "ssesolve_jc", "smesolve_jc"])
     ap.add_argument("--rates", default="10,30,100,300")
     ap.add_argument("--requests", type=int, default=120)
@@ -511,6 +518,360 @@ def run_ising10(args):
     g.free()
 
 
+C2_NTRAJ = 2000
+# algorithmic bytes of the mixed wide trajectory kernel per row and attempted
+# step (second-order increment form): stages 2-6 read f or f2 and the
+# remainders and write one remainder (128 B in all); stage 7 reads y, f
+# (hi + lo), f2 and r_3..r_6 (72 B), writes y_new, its FP32 remainder, the
+# error partial and scale (36 B), then f_new (hi + lo) after reading the
+# partial and scale back (28 B); plus one gather row of the remainder (8 B)
+MW_BYTES_PER_ROW = 280.0
+C2_SEED = 3            # Philox key of the 14-spin trajectories
+C2_TOL = dict(precision="mixed", rtol=1e-7, atol=1e-9)
+C2_WORKLOAD = ("ising_c2: dissipative transverse-field Ising chains, J=1, h=U[0.5,1.5] seed 3, "
+               "gamma=0.1, all spins excited, t in [0,10], 100 saveat, e_ops Sx Sy Sz, mixed "
+               "precision (FP32 RHS, FP64 state / controller / jumps), rtol 1e-7 atol 1e-9: "
+               "mesolve of 10 spins (rho with 2^20 entries, grid kernel) then mcsolve of 14 "
+               "spins (n = 16384) with 2000 trajectories (Philox seed 3), one stream")
+
+
+def _hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+_C2_WORKER = {}
+
+
+def _c2_traj_worker(j):
+    """One oracle trajectory of the 14-spin chain (spawned worker process,
+    single-threaded); returns its wall time in seconds."""
+    if "s" not in _C2_WORKER:
+        _C2_WORKER["s"] = W.ising_chain(14)
+    from oracle.mcsolve import mcsolve as o_mc
+    s = _C2_WORKER["s"]
+    t0 = time.perf_counter()
+    o_mc(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=1, seed=C2_SEED, traj_ids=[j],
+         rtol=C2_TOL["rtol"], atol=C2_TOL["atol"])
+    return time.perf_counter() - t0
+
+
+def c2_cpu_sample(rhs_me, per_core=2, small=False):
+    """The FP64 oracle, as it stands, on a bounded sample of the ising_c2 job:
+    its 10-spin mesolve over the first output interval (Liouvillian build
+    included) and `per_core` 14-spin trajectories per host core in a spawned
+    process pool (one single-threaded process per core).  The full job is
+    estimated as: Liouvillian build + time per RHS evaluation x rhs_me (the
+    RHS count of the full mesolve) + the mean trajectory time x 2000, the
+    trajectories spread over the cores (all-core) or run one after another
+    (single core)."""
+    import multiprocessing as mp
+    from oracle.lindblad import liouvillian
+    from oracle.mesolve import mesolve as o_me
+    cores = os.cpu_count() or 1
+    s10 = W.ising_chain(10)
+    t0 = time.perf_counter()
+    liouvillian(s10.H, s10.c_ops)
+    t_build = time.perf_counter() - t0
+    tl = s10.tlist[:2] if not small else np.array([0.0, s10.tlist[1] * 0.05])
+    t0 = time.perf_counter()
+    r = o_me(s10.H, s10.c_ops, s10.e_ops, s10.psi0, tl, rtol=C2_TOL["rtol"], atol=C2_TOL["atol"])
+    t_me = time.perf_counter() - t0
+    per_rhs = max(t_me - t_build, 1e-9) / r["stats"]["rhs_evals"]
+    me_est = t_build + per_rhs * rhs_me
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    ntr = max(1, cores * per_core) if not small else 1
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(cores, ntr)) as pool:
+        ttimes = pool.map(_c2_traj_worker, range(ntr))
+    t_pool = time.perf_counter() - t0
+    traj_mean = statistics.mean(ttimes)
+    job_all = me_est + traj_mean * C2_NTRAJ / cores
+    job_one = me_est + traj_mean * C2_NTRAJ
+    return dict(value_all=rhs_me / job_all, value_one=rhs_me / job_one, cores=cores,
+                job_all_s=job_all, job_one_s=job_one, traj_mean_s=traj_mean, ntraj=ntr,
+                t_pool_s=t_pool, me_sample_s=t_me, build_s=t_build, rhs_sample=r["stats"]["rhs_evals"],
+                per_rhs_s=per_rhs, wall_s=t_me + t_build + t_pool)
+
+
+def _c2_sample_text(c):
+    return (f"oracle (FP64 NumPy/SciPy, as it stands): 10-spin mesolve over the first output interval "
+            f"({c['rhs_sample']} RHS evaluations, {c['per_rhs_s']:.3f} s each, Liouvillian build "
+            f"{c['build_s']:.1f} s) scaled to the full solve's RHS count, plus {c['ntraj']} of the 2000 "
+            f"14-spin trajectories ({c['traj_mean_s']:.2f} s each, one single-threaded spawned process "
+            f"per core) scaled to 2000 over {c['cores']} cores")
+
+
+def c2_reference_rhs():
+    """RHS evaluations of the full 10-spin mesolve, for scaling the oracle's
+    sample when no GPU run has counted them (the count the adaptive solve
+    takes with these tolerances, 347 accepted steps x 6 + 2)."""
+    return 2084
+
+
+def run_c2_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        c2_cpu_sample(c2_reference_rhs(), small=True)
+    vals, jobs, last = [], [], None
+    for _ in range(args.steps):
+        last = c2_cpu_sample(c2_reference_rhs(), per_core=1)
+        vals.append(last["value_all"])
+        jobs.append(last["job_all_s"])
+    v = statistics.mean(vals)
+    print(json.dumps({
+        "metric": "Lindblad RHS evals/s of the ising_c2 job (10-spin mesolve + 14-spin 2000-trajectory "
+                  "mcsolve per step), with mcsolve traj/s",
+        "value": v, "unit": "RHS evals/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(jobs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": C2_WORKLOAD},
+        "mcsolve_traj_per_s": C2_NTRAJ / statistics.mean(jobs),
+        "cpu_baseline": {"value": v, "unit": "RHS evals/s", "cores": last["cores"], "kind": "oracle",
+                         "sample": _c2_sample_text(last)},
+        "e2e": {"value": v, "unit": "RHS evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(q * len(xs)))]
+
+
+def c0_latency(qtl, dev, nsolves=20):
+    """Single-solve latency of the driven damped cavity (N = 20, FP64 Tsit5,
+    rtol 1e-8 atol 1e-10, 201 output times) on the cluster kernel: p50/p99
+    over back-to-back solves timed with CUDA events."""
+    import torch
+    s = W.driven_cavity()
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    rho0 = torch.from_numpy(np.outer(s.psi0, s.psi0.conj()).reshape(-1, order="F").copy()).to(dev)
+    tl = torch.from_numpy(s.tlist).to(dev)
+    ex = torch.zeros((2, len(s.tlist)), dtype=torch.complex128, device=dev)
+    info = torch.zeros(5, dtype=torch.int64, device=dev)
+    main = torch.cuda.current_stream(dev)
+    o = qtl.make_opts(rtol=s.rtol, atol=s.atol, stream=main.cuda_stream)
+    ms = []
+    for k in range(nsolves + 3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        qtl.mesolve_async(g.handle, rho0, 0, tl, o, ex, None, info)
+        e1.record(main)
+        torch.cuda.synchronize(dev)
+        if k >= 3:
+            ms.append(e0.elapsed_time(e1))
+    inf = info.cpu().numpy()
+    g.free()
+    return {"workload": "driven cavity N=20 FP64 mesolve, 201 saveat", "p50_ms": _pct(ms, 0.5),
+            "p99_ms": _pct(ms, 0.99), "solves": nsolves, "rhs_evals": int(inf[3]),
+            "rhs_evals_per_s": int(inf[3]) / (statistics.median(ms) / 1e3)}
+
+
+def c1_job(qtl, dev, steps=3):
+    """The Jaynes-Cummings job (N = 40 x 2, FP64 mesolve + 1000 FP64
+    trajectories on two concurrent streams), a few timed steps."""
+    import torch
+    s = workload()
+    n_e, nt = len(s.e_ops), len(s.tlist)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    psi = torch.from_numpy(s.psi0).to(dev)
+    tl = torch.from_numpy(s.tlist).to(dev)
+    ex1 = torch.zeros((n_e, nt), dtype=torch.complex128, device=dev)
+    ex2 = torch.zeros((n_e, nt), dtype=torch.complex128, device=dev)
+    i1 = torch.zeros(5, dtype=torch.int64, device=dev)
+    i2 = torch.zeros(5, dtype=torch.int64, device=dev)
+    a, b = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    main = torch.cuda.current_stream(dev)
+    oa = qtl.make_opts(rtol=s.rtol, atol=s.atol, stream=a.cuda_stream)
+    ob = qtl.make_opts(rtol=s.rtol, atol=s.atol, stream=b.cuda_stream)
+    ms = []
+    for k in range(steps + 2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        a.wait_event(e0)
+        b.wait_event(e0)
+        qtl.mesolve_async(g.handle, psi, 1, tl, oa, ex1, None, i1)
+        qtl.mcsolve_async(g.handle, psi, tl, NTRAJ, SEED, ob, ex2, None, i2)
+        main.wait_stream(a)
+        main.wait_stream(b)
+        e1.record(main)
+        torch.cuda.synchronize(dev)
+        if k >= 2:
+            ms.append(e0.elapsed_time(e1))
+    rhs = int(i1.cpu().numpy()[3])
+    g.free()
+    m = statistics.mean(ms)
+    return {"workload": "jc_40x2 FP64 mesolve + 1000 FP64 trajectories, concurrent streams",
+            "ms_per_step": m, "rhs_evals_per_s": rhs / (m / 1e3), "traj_per_s": NTRAJ / (m / 1e3)}
+
+
+def run_c2(args):
+    """The default job (ising_c2, the largest single-GPU configuration): per
+    step one mixed-precision mesolve of the 10-spin chain (grid kernel, a
+    density matrix with 2^20 entries) followed on the same stream by one
+    mixed-precision mcsolve of the 14-spin chain with 2000 trajectories (wide
+    trajectory kernel).  Value: Lindblad RHS evaluations of the step's
+    mesolve per second of the whole step; mcsolve trajectories per second of
+    the whole step beside it; each solve's own rate and p50/p99 latency in
+    `phases`.  Roofline: the dominant kernel (mc_wide_kernel, 280 B of state
+    per row and attempted step) against the measured copy bandwidth; the
+    grid kernel's own figure (400 B per entry and attempted step) in
+    `kernels`."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2504_21440_gb300 import qtl
+    qtl.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    s10, s14 = W.ising_chain(10), W.ising_chain(14)
+    g10 = qtl.System(s10.H, s10.c_ops, s10.e_ops)
+    g14 = qtl.System(s14.H, s14.c_ops, s14.e_ops)
+    nt = len(s10.tlist)
+    psi10 = torch.from_numpy(s10.psi0).to(dev)
+    psi14 = torch.from_numpy(s14.psi0).to(dev)
+    tl = torch.from_numpy(s10.tlist).to(dev)
+    ex10 = torch.zeros((3, nt), dtype=torch.complex128, device=dev)
+    ex14 = torch.zeros((3, nt), dtype=torch.complex128, device=dev)
+    tex = torch.zeros((3, nt, C2_NTRAJ), dtype=torch.complex128, device=dev)
+    i10 = torch.zeros(5, dtype=torch.int64, device=dev)
+    i14 = torch.zeros(5, dtype=torch.int64, device=dev)
+    main = torch.cuda.current_stream(dev)
+    o = qtl.make_opts(stream=main.cuda_stream, **C2_TOL)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def step():
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(main)
+        qtl.mesolve_async(g10.handle, psi10, 1, tl, o, ex10, None, i10)
+        e[1].record(main)
+        qtl.mcsolve_async(g14.handle, psi14, tl, C2_NTRAJ, C2_SEED, o, ex14, tex, i14)
+        e[2].record(main)
+        return e
+
+    for _ in range(args.warmup):
+        step()
+        torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = qtl.launch_count()
+    me_ms, mc_ms, job_ms, att_me, att_mc = [], [], [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        e = step()
+        torch.cuda.synchronize(dev)
+        me_ms.append(e[0].elapsed_time(e[1]))
+        mc_ms.append(e[1].elapsed_time(e[2]))
+        job_ms.append(e[0].elapsed_time(e[2]))
+        a, b = i10.cpu().numpy(), i14.cpu().numpy()
+        att_me.append(int(a[1] + a[2]))
+        att_mc.append(int(b[1] + b[2]))
+    torch.cuda.synchronize(dev)
+    launches = qtl.launch_count() - l0
+    clk = clocks.stop()
+    total_ms = sum(job_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    a, b = i10.cpu().numpy(), i14.cpu().numpy()
+    st10 = dict(steps_acc=int(a[1]), steps_rej=int(a[2]), rhs_evals=int(a[3]))
+    st14 = dict(steps_acc=int(b[1]), steps_rej=int(b[2]), rhs_evals=int(b[3]), jumps=int(b[4]))
+    status = [int(a[0]) & 0xffffffff, int(b[0]) & 0xffffffff]
+    ms_per_step = total_ms / args.steps
+    value = world * st10["rhs_evals"] / (ms_per_step / 1e3)
+    peak, peak_src = _hbm_peak()
+    k_me, k_mc = statistics.mean(me_ms), statistics.mean(mc_ms)
+    gb_mc = MW_BYTES_PER_ROW * s14.n * statistics.mean(att_mc) / 1e9
+    gb_me = 400.0 * s10.n * s10.n * statistics.mean(att_me) / 1e9
+    ach_mc, ach_me = gb_mc / (k_mc / 1e3), gb_me / (k_me / 1e3)
+    tr_mc = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", "mc_wide.cuh"),
+                                 os.path.join(ROOT, "profiles", "mc_wide_kernel_ising14_mixed.md"))
+    tr_me = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", "me_grid.cu"),
+                                 os.path.join(ROOT, "profiles", "me_grid_kernel_ising10_mixed.md"))
+    roof = {"bound": "hbm", "achieved": ach_mc, "peak": peak, "unit": "GB/s", "frac": ach_mc / peak,
+            "traffic": tr_mc, "kernel": "mc_wide_kernel", "peak_source": f"hbm_gbs ({peak_src})",
+            "algorithmic_bytes_per_launch": gb_mc * 1e9,
+            "model": "280 B of trajectory state per row per attempted step (increment form)"}
+    kernels = {"mc_wide_kernel": {"ms": k_mc, "gb_s": ach_mc, "frac": ach_mc / peak, "traffic": tr_mc},
+               "me_grid_kernel": {"ms": k_me, "gb_s": ach_me, "frac": ach_me / peak, "traffic": tr_me,
+                                  "model": "400 B per rho entry per attempted step"}}
+    out = None
+    if rank == 0:
+        # the reduced-precision results against FP64 (host API with the FP64
+        # shadow; outside the timed region): the full mesolve, and the first
+        # 152 trajectories (one per SM) of the mcsolve
+        r10 = qtl.mesolve(g10.handle, 3, s10.psi0, s10.tlist, qtl.make_opts(shadow_fp64=True, **C2_TOL))
+        r14 = qtl.mcsolve(g14.handle, 3, s14.psi0, s14.tlist, 152, C2_SEED,
+                          qtl.make_opts(shadow_fp64=True, **C2_TOL))
+        err = {"mesolve_ising10": r10["stats"]["err_vs_fp64"],
+               "mcsolve_ising14_first152traj": r14["stats"]["err_vs_fp64"]}
+        e2e = None
+        if not args.no_e2e:
+            walls = []
+            o_host = qtl.make_opts(stream=main.cuda_stream, **C2_TOL)
+            for k in range(3):
+                t0 = time.perf_counter()
+                qtl.mesolve(g10.handle, 3, s10.psi0, s10.tlist, o_host)
+                qtl.mcsolve(g14.handle, 3, s14.psi0, s14.tlist, C2_NTRAJ, C2_SEED, o_host)
+                if k > 0:
+                    walls.append(time.perf_counter() - t0)
+            w = statistics.mean(walls)
+            e2e = {"value": st10["rhs_evals"] / w, "unit": "RHS evals/s",
+                   "h2d_bytes_per_step": (s10.n + s14.n) * 16 + 2 * nt * 8,
+                   "d2h_bytes_per_step": 2 * (3 * nt * 16 + 40), "ms_per_step": 1e3 * w,
+                   "mcsolve_traj_per_s": C2_NTRAJ / w,
+                   "path": "host-pointer qtl_mesolve then qtl_mcsolve, copies inside the timed region"}
+        c0 = c0_latency(qtl, dev)
+        c1 = c1_job(qtl, dev)
+        cpu = None
+        if not args.no_cpu_baseline:
+            c = c2_cpu_sample(st10["rhs_evals"])
+            cpu = {"value": c["value_all"], "unit": "RHS evals/s", "cores": c["cores"], "kind": "oracle",
+                   "sample": _c2_sample_text(c), "single_core_value": c["value_one"],
+                   "job_s_all_cores": c["job_all_s"], "job_s_single_core": c["job_one_s"],
+                   "mcsolve_traj_per_s_all_cores": C2_NTRAJ / c["job_all_s"]}
+        out = {"metric": "Lindblad RHS evals/s of the ising_c2 job (10-spin mesolve + 14-spin 2000-trajectory "
+                         "mcsolve per step), with mcsolve traj/s",
+               "value": value, "unit": "RHS evals/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32 RHS / f64 state (mixed)",
+               "data": "synthetic",
+               "config": {"workload": C2_WORKLOAD,
+                          "l2": "flushed (512 MB write) between timed steps; 14-spin state 290 MB > L2",
+                          "parallelism": f"independent job per GPU x{world}"},
+               "mcsolve_traj_per_s": world * C2_NTRAJ / (ms_per_step / 1e3),
+               "phases": {"mesolve_ising10": {"ms_mean": k_me, "p50_ms": _pct(me_ms, 0.5), "p99_ms": _pct(me_ms, 0.99),
+                                              "rhs_evals": st10["rhs_evals"],
+                                              "rhs_evals_per_s": st10["rhs_evals"] / (k_me / 1e3)},
+                          "mcsolve_ising14": {"ms_mean": k_mc, "p50_ms": _pct(mc_ms, 0.5), "p99_ms": _pct(mc_ms, 0.99),
+                                              "traj_per_s": C2_NTRAJ / (k_mc / 1e3),
+                                              "attempted_steps_per_traj": statistics.mean(att_mc) / C2_NTRAJ}},
+               "latency_ms": {"p50": _pct(job_ms, 0.5), "p99": _pct(job_ms, 0.99)},
+               "err_vs_fp64": err, "Sz_t10": {"ising10": float(ex10[2, -1].real), "ising14": float(ex14[2, -1].real)},
+               "status": status, "stats": {"mesolve": st10, "mcsolve": st14},
+               "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+               "c0_single_solve_latency": c0, "c1_job": c1,
+               "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    g10.free()
+    g14.free()
+
+
 def run_ising14_mc(args):
     """mcsolve on the dissipative transverse-field Ising chain of 14 spins
     (n = 16,384; H_eff with 245,760 entries), h from seed 3, gamma = 0.1, all
@@ -518,13 +879,9 @@ def run_ising14_mc(args):
     precision, rtol 1e-7, atol 1e-9: one mcsolve (the wide trajectory kernel,
     one 1024-thread CTA per trajectory) per step.  Value: trajectories per
     second.  Roofline: the integrator's state bytes per attempted step and row
-    -- per stage s < 6 the FP32 state copy (8 B) and s derivatives (8 B each)
-    read and the new derivative written (8 B); at the sixth stage the FP64
-    state read and y_new written (2 x 16 B), its FP32 copy (8 B), 6
-    derivatives read (48 B), the error partial and scale written and read
-    back (2 x 12 B) and the last derivative written (8 B) -- 320 B in all,
-    against the measured copy bandwidth (H_eff itself is shared by all
-    trajectories and stays in L2)."""
+    in the second-order increment form (MW_BYTES_PER_ROW, 280 B) against the
+    measured copy bandwidth (H_eff itself is shared by all trajectories and
+    stays in L2)."""
     import torch
     from paper_2504_21440_gb300 import qtl
     torch.cuda.set_device(0)
@@ -568,7 +925,7 @@ def run_ising14_mc(args):
     except OSError:
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = 320.0 * s.n * statistics.mean(atts) / (mean_ms / 1e3) / 1e9
+    achieved = MW_BYTES_PER_ROW * s.n * statistics.mean(atts) / (mean_ms / 1e3) / 1e9
     traffic = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", "mc_wide.cuh"),
                                    os.path.join(ROOT, "profiles", "mc_wide_kernel_ising14_mixed.md"))
     print(json.dumps({
@@ -583,7 +940,7 @@ def run_ising14_mc(args):
         "status": int(inf[0]) & 0xffffffff, "Sz_t10": float(ex[2, -1].real),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "mc_wide_kernel",
-                     "note": "algorithmic 320 B/row/attempt of state; latency-bound (see profiles)"},
+                     "note": "algorithmic 280 B/row/attempt of state (increment form); latency-bound (see profiles)"},
         "gpu_launches": launches, "clocks": clk}))
     g.free()
 
@@ -891,6 +1248,12 @@ SHARDED = ("jc_40x2", "kerr_sweep_1024")
 
 def main():
     args = parse()
+    if args.workload == "ising_c2":
+        if args.impl == "reference":
+            run_c2_reference(args)
+        else:
+            run_c2(args)
+        return
     if args.impl == "reference" and args.workload != "jc_40x2":
         # the other workloads time the oracle in their own cpu_baseline entry
         sys.exit("bench.py: --impl reference times the jc_40x2 job; the line of --workload %s "

@@ -97,7 +97,15 @@ enum { QTL_FP64 = 0, QTL_MIXED = 1 };
  *                 over a cooperative grid; no Liouvillian is formed).
  *                 mcsolve: AUTO (trajectory state in registers up to n = 1024,
  *                 else in global memory), CLUSTER (registers; QTL_ETOOBIG
- *                 above n = 1024) or GRID (global memory at any n) */
+ *                 above n = 1024) or GRID (global memory at any n)
+ *   shadow_fp64   0 or 1.  With QTL_MIXED, 1 makes the host-pointer calls
+ *                 qtl_mesolve and qtl_mcsolve, and server requests, run the
+ *                 same solve a second time with precision QTL_FP64 (all other
+ *                 options equal, the same seed) and report the largest
+ *                 |difference| of their expectation values in
+ *                 qtl_stats.err_vs_fp64: the reduced-precision result's error
+ *                 against FP64, per result.  It roughly doubles the call's
+ *                 cost.  Ignored by the _async calls, batches and plans. */
 enum { QTL_ENGINE_AUTO = 0, QTL_ENGINE_CLUSTER = 1, QTL_ENGINE_GRID = 2 };
 typedef struct {
     int32_t method;
@@ -112,15 +120,22 @@ typedef struct {
     double dt_fixed;
     void* cuda_stream;
     int32_t engine;
-    int32_t reserved;
+    int32_t shadow_fp64;
 } qtl_opts;
 
-/* Counters of one solve (summed over trajectories for mcsolve). */
+/* Counters of one solve (summed over trajectories for mcsolve), and
+ * err_vs_fp64: max over observables and times of |expect - expect_FP64| for
+ * a QTL_MIXED solve run with opts.shadow_fp64 = 1 (for mcsolve the FP64
+ * trajectories use the same random draws, so the difference also holds the
+ * rare trajectories whose jump decisions the FP32 rounding moved); 0 for a
+ * QTL_FP64 solve; -1 when not computed (QTL_MIXED without the shadow, or a
+ * shadow solve that failed). */
 typedef struct {
     int64_t steps_acc;
     int64_t steps_rej;
     int64_t rhs_evals;
     int64_t jumps;
+    double err_vs_fp64;
 } qtl_stats;
 
 /* Device-resident status of an _async solve: status is a qtl_status. */
@@ -355,6 +370,84 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
                              int32_t nt, int32_t ntraj, uint64_t seed, int64_t traj_offset,
                              const qtl_opts* opts, qtl_c128* expect_dev,
                              qtl_c128* traj_expect_dev, qtl_device_info* info_dev);
+
+/* ------------------------------------------------------ stationary states ---
+ * steadystate (Sec. 3.2): the density matrix with L vec(rho) = 0 and
+ * Tr rho = 1.  steadystate_fourier (Appendix A): the Fourier components
+ * rho_k, k = -nmax..nmax, of the periodic long-time state under
+ * H(t) = H0 + F cos(omega t) X (H0 and the collapse operators are the
+ * system's), from the block-tridiagonal system
+ *   (L0 - i k omega) rho_k + L1 (rho_{k-1} + rho_{k+1}) = 0,
+ *   L1 = -i [(F/2) X, .],  components beyond nmax taken as zero,
+ * with Tr rho_0 = 1 in place of the first equation of the k = 0 block.
+ * The paper solves these directly; here they are solved on the GPU by
+ * flexible GMRES(restart) with classical Gram-Schmidt applied twice, right-
+ * preconditioned by the inverse of the no-jump part of each diagonal block,
+ * X -> A X + X A^H - i k omega X with A = -i H_eff, applied through the
+ * eigendecomposition A = V diag(lambda) V^-1 (computed once per system on
+ * the host in FP64, O(n^3): about a minute at n = 1024) as four dense
+ * complex GEMMs per block.  Everything is FP64.
+ *   rho_out: steadystate: vec(rho)[n*n] column-major; steadystate_fourier:
+ *            [(2 nmax + 1) * n * n], block a = vec(rho_{a - nmax}).
+ *   X: an operator of the system's dimension (CSR or dense); nmax <= 64.
+ * n <= QTL_SS_MAX_N (QTL_ETOOBIG above); systems with time-dependent terms
+ * are refused (QTL_EINVAL).  Host pointers; returns when done, on
+ * opts->cuda_stream.  QTL_ESTEP when the GMRES residual |b - M x| / |b| has
+ * not reached opts->tol within opts->max_iter preconditioned products (the
+ * last iterate is still written), QTL_ESTEP too if the eigendecomposition
+ * does not converge. */
+#define QTL_SS_MAX_N 1024
+typedef struct {
+    double tol;          /* relative GMRES residual (default 1e-12) */
+    int32_t restart;     /* Krylov vectors per cycle, 1..512 (default 60) */
+    int32_t max_iter;    /* preconditioned matrix-vector products at most (default 20000) */
+    void* cuda_stream;   /* cudaStream_t, NULL = the legacy default stream */
+} qtl_ss_opts;
+typedef struct {
+    int32_t iterations;      /* preconditioned matrix-vector products */
+    int32_t pad;
+    double residual;         /* |M x - b|_2 / |x|_2 of the returned vector (M: the system with the trace row) */
+    double cond_v;           /* ||V||_F ||V^-1||_F / n for the eigenvectors of A (1 for orthonormal V) */
+    double gmres_residual;   /* |b - M x| / |b| at the last iteration */
+} qtl_ss_stats;
+void qtl_ss_opts_default(qtl_ss_opts* opts);
+qtl_status qtl_steadystate(qtl_system* sys, const qtl_ss_opts* opts, qtl_c128* rho_out, qtl_ss_stats* stats);
+qtl_status qtl_steadystate_fourier(qtl_system* sys, const qtl_op* X, double F, double omega, int32_t nmax,
+                                   const qtl_ss_opts* opts, qtl_c128* rho_out, qtl_ss_stats* stats);
+
+/* ------------------------------------------- dynamical shifted Fock ---
+ * dsf_mesolve (Sec. 3.6; Appendix B, Algorithm 1): the master equation in a
+ * frame displaced by a tracked coherence alpha_k of each DSF mode, so that a
+ * small Fock cutoff holds the fluctuations around a large coherent state.
+ * The operators are functions of the shifted mode operators a_k + alpha_k I
+ * (as in the paper, where H, c_ops and e_ops are functions of op_list): the
+ * library calls build(alpha, n_modes, user, &sys) whenever alpha changes and
+ * frees the system it returns; build creates it with qtl_system_create from
+ * operators in which every a_k is replaced by a_k + alpha_k I, and returns
+ * QTL_OK.
+ * At every time of tlist (the check interval of Algorithm 1 is tlist's
+ * spacing): the state is integrated from the previous time by qtl_mesolve's
+ * kernels (opts as for qtl_mesolve; adaptive steps between checks), the
+ * observables are recorded, then for each mode d_k = Tr(rho a_k) is
+ * computed and, when |d_k| > threshold, rho <- D rho D^H with
+ * D = exp(-d_k a_k^H + conj(d_k) a_k) exponentiated in the truncated space,
+ * alpha_k += d_k, and the system is rebuilt.  The state stays on the device.
+ *   modes[n_modes]   a_k on the full space (n x n), 1 <= n_modes <= 16
+ *   alpha0[n_modes]  initial coherences; state0: ket (is_ket = 1, n entries)
+ *                    or vec(rho0) (n*n), in the frame displaced by alpha0
+ *   n_e              observables of the systems build returns (checked)
+ *   expect_out[n_e*nt]   observables at each time (before that time's shift)
+ *   alpha_out[n_modes*nt] (or NULL): alpha_k after each time's shift
+ *   shifts (or NULL): number of displacements applied
+ * Host pointers; returns when done.  Errors: QTL_EINVAL (arguments, a built
+ * system of another dimension, observable count or with time-dependent
+ * terms), build's own status, the solve's status (QTL_ESTEP), QTL_ENOMEM,
+ * QTL_ECUDA. */
+typedef qtl_status (*qtl_dsf_build_fn)(const qtl_c128* alpha, int32_t n_modes, void* user, qtl_system** out);
+qtl_status qtl_dsf_mesolve(qtl_dsf_build_fn build, void* user, int32_t n_modes, const qtl_op* modes,
+                           const qtl_c128* alpha0, const qtl_c128* state0, int32_t is_ket, const double* tlist,
+                           int32_t nt, double threshold, const qtl_opts* opts, int32_t n_e, qtl_c128* expect_out,
+                           qtl_c128* alpha_out, int32_t* shifts, qtl_stats* stats);
 
 /* ------------------------------------------------------------- serving ---
  * A request server (no counterpart in the paper; it serves the mesolve and

@@ -69,6 +69,8 @@ struct DevSell {
     float* vs32 = nullptr;
     double2* vc64 = nullptr; // [nvc] complex values
     float2* vc32 = nullptr;
+    float* vs32lo = nullptr; // v - (double)(float)v: the FP32 remainder of each value
+    float2* vc32lo = nullptr;
     std::vector<int4> hdesc; // host copy of the descriptors when there are few
 };
 
@@ -127,6 +129,7 @@ struct System {
     double2* cval64 = nullptr;  // [n_c][n] its value (only when every row has <= 1 entry)
     float2* cval32 = nullptr;
     int device = 0;
+    struct SsCache* ss = nullptr;   // stationary-state preconditioner (steady.cu), built on first use
 };
 
 // -------------------------------------------- device-side solve descriptors
@@ -261,10 +264,13 @@ struct McJob {
     const float* svs32;
     const double2* svc64;
     const float2* svc32;
+    const float* svs32lo;  // FP32 remainders of the values (error-free products, mixed precision)
+    const float2* svc32lo;
     unsigned char* wscr;   // [grid][wstride] bytes of per-CTA state
     size_t wstride;
     int xsmem;             // stage inputs in shared memory (1) or in wscr (0)
     int xbufs;             // stage-input buffers in shared memory (1 or 2)
+    int* wnext;            // trajectory counter (zero at launch), or null: static assignment
 };
 
 // Launch plan of the wide trajectory kernel: grid, shared memory and the
@@ -318,6 +324,14 @@ cudaError_t qtl_malloc_async(void** p, size_t bytes, cudaStream_t st);
 
 void count_launch(int k = 1);
 void set_cuda_error(cudaError_t e);
+
+// runtime.cpp helpers for the other translation units
+qtl_status op_to_csr(const qtl_op* op, int n_expect, Csr& out);
+qtl_status csr_upload(const Csr& m, DevCsr& d);
+void csr_free(DevCsr& d);
+void ss_cache_free(System& s);   // steady.cu
+// C = op(A) op(B), n x n complex FP64, column-major, op: 0 identity, 1 conjugate transpose (steady.cu)
+cudaError_t launch_zgemm(int n, const double2* A, int ta, const double2* B, int tb, double2* C, cudaStream_t st);
 
 }  // namespace qtl
 

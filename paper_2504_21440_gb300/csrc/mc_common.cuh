@@ -185,6 +185,12 @@ struct McCtl {
     // are separate because a landing step is followed at once by the next
     // action, which may be a repeat of the same time.
     int action, land, accept, save, rsave, ch, rootgo, pub;
+    // second-order increment form of the wide kernel's mixed precision:
+    // htry (FP64 and FP32), htry^2 sum_j b_j c_j, htry^2 sum_j e_j c_j,
+    // htry^2 e_7, and htry^2 W_s with W_s = sum_{l<s} a_sl c_l
+    double hd, c2b;
+    float hf, c2e, he7h;
+    float c2w[7];
     float wf[MC_MAXWARPS];
     double wd[MC_MAXWARPS];
     // time-dependent terms: f_k at the stage times t + c_s htry (slots 1..6)

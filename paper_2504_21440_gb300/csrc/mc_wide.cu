@@ -56,7 +56,7 @@ cudaError_t mc_wide_plan(const McJob& J, int precision, McWidePlan* p) {
     if (grid > J.ntraj) grid = J.ntraj;
     p->grid = grid;
     p->stride = mw_vec_bytes(J.n) * (size_t)(MW_NV + (p->xsmem ? 0 : 2));
-    p->scratch_bytes = p->stride * (size_t)grid;
+    p->scratch_bytes = p->stride * (size_t)grid + 256;  // + the trajectory counter
     return cudaSuccess;
 }
 
@@ -67,6 +67,10 @@ cudaError_t launch_mc_wide(const McJob& J0, int precision, const McWidePlan& p, 
     J.wstride = p.stride;
     J.xsmem = p.xsmem;
     J.xbufs = p.xbufs;
+    // the trajectory counter sits after the CTAs' slices
+    J.wnext = (int*)((unsigned char*)scratch + p.stride * (size_t)p.grid);
+    cudaError_t e = cudaMemsetAsync(J.wnext, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     count_launch();
     // explicit columns are 32-bit (the 16-bit form cut bytes only in
     // explicit groups and doubled the instantiations)

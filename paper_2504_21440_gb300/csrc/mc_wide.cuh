@@ -35,17 +35,35 @@ namespace qtl {
 #define QTL_MW_THREADS 1024
 #endif
 constexpr int MW_T = QTL_MW_THREADS;
-constexpr int MW_NV = 13;                   // vectors in a CTA's scratch slice
+constexpr int MW_NV = 14;                   // vectors in a CTA's scratch slice
 constexpr size_t MW_SMEM_X_MAX = 200 * 1024;  // shared-memory budget for stage inputs
 
 // Slots of a CTA's scratch slice, each mw_vec_bytes(n) bytes (256-aligned):
 //   0,1    y / y_new, complex128 (the roles swap on accept)
-//   2,3    FP32 copies of y / y_new (mixed precision only)
-//   4..10  k_1..k_7 (complex128, or complex64 in mixed precision); k_1 and
-//          k_7 trade slots 4 and 10 on accept (FSAL)
-//   11     partial error estimate sum_{j<7} h e_j k_j of the sixth pass
+//   2,3    mixed precision: f = A y and f_new = A y_new as FP32 pairs (the
+//          hi parts, then the lo parts; the roles swap with y / y_new)
+//   4..10  FP64: k_1..k_7 (complex128); k_1 and k_7 trade slots 4 and 10 on
+//          accept (FSAL).  Mixed precision: slot 5 holds f2 = A f (stage 2)
+//          and slots 6..9 the remainders r_3..r_6 (complex64)
+//   11     partial error estimate of the sixth pass
 //   12     its scale sc_i = atol + rtol max(|y_i|, |y_new,i|) (float)
-//   13,14  the two stage inputs, when they do not fit in shared memory
+//   13     mixed precision: the FP32 remainder y_new - (float)y_new
+//   14,15  the two stage inputs, when they do not fit in shared memory
+//
+// Mixed precision is a second-order increment form.  With f = A y and
+// f2 = A f, every stage derivative is k_s = f + h c_s f2 + r_s, where
+// r_s = A d_s, d_s = x_s - y - h c_s f = h^2 W_s f2 + h sum_{l<s} a_sl r_l
+// (W_s = sum_l a_sl c_l, r_1 = r_2 = 0).  The FP32 operator then acts on f
+// (stage 2, giving f2) and on the O(h^2) increments d_s (stages 3-6); the
+// new state y_new = y + h f + h^2 (sum b c) f2 + h sum b_j r_j is formed in
+// FP64, and the last stage evaluates f_new = A y_new with error-free FP32
+// products and sums (sell_row_dd), which is the next step's f.  FP32
+// rounding therefore enters only through terms of order h^2 |A|^2 |y|:
+// with the plain FP32 right-hand side the 14-spin chain's trajectories
+// differed from FP64 by 4e-6 on Sz; rounding the operator or the stage
+// coefficients to FP32 shifts the method's frequencies, which accumulates
+// over the span.  The error estimate is h^2 (sum e c) f2 + h sum e_j r_j
+// (sum e_j = 0), with r_7 = f_new - f - h f2.
 __host__ __device__ inline size_t mw_vec_bytes(int n) {
     return ((size_t)n * 16 + 255) & ~(size_t)255;
 }
@@ -245,6 +263,138 @@ __device__ __forceinline__ T2 sell_row(int q, const int4* __restrict__ sl,
     return acc;
 }
 
+// ---- error-free row products (the base derivative of the mixed precision) ----
+// s + c += (a + al) (x + xl) with the product a x exact (TwoProduct by FMA)
+// and its addition to s exact (Knuth's TwoSum); the small cross terms a xl +
+// al x and the rounding errors go to c.  The _rn intrinsics keep the
+// compiler from contracting the multiply into the additions, which would
+// break the error-free transformations.
+__device__ __forceinline__ void dd_acc(float& s, float& c, float a, float x, float al, float xl) {
+    const float p = __fmul_rn(a, x);
+    const float e = __fmaf_rn(a, x, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fmaf_rn(al, x, __fmaf_rn(a, xl, __fadd_rn(__fadd_rn(c, err), e)));
+}
+
+// One group of a row, as sell_group, with the values (vh + vl) and the input
+// (gx(c) + gl(c)) both given as FP32 pairs; accumulates into the pairs
+// (rs, rc) (real part) and (is, ic) (imaginary part).
+template <int G, class IT, class GX, class GL, class DG>
+__device__ __forceinline__ void sell_group_dd(int q, int lane, int w, int type, DG&& dg, int cbase,
+                                              int vbase, const IT* __restrict__ ci,
+                                              const float* __restrict__ vs, const float2* __restrict__ vc,
+                                              const float* __restrict__ vsl, const float2* __restrict__ vcl,
+                                              GX&& gx, GL&& gl, unsigned long long pol, float& rs,
+                                              float& rc, float& is, float& ic) {
+    auto acc_s = [&](int c, float vh, float vl) {
+        const float2 x = gx(c), xl = gl(c);
+        if constexpr (G == 0) {
+            dd_acc(rs, rc, vh, x.x, vl, xl.x);
+            dd_acc(is, ic, vh, x.y, vl, xl.y);
+        } else {
+            dd_acc(rs, rc, -vh, x.y, -vl, xl.y);
+            dd_acc(is, ic, vh, x.x, vl, xl.x);
+        }
+    };
+    auto acc_c = [&](int c, float2 vh, float2 vl) {
+        const float2 x = gx(c), xl = gl(c);
+        dd_acc(rs, rc, vh.x, x.x, vl.x, xl.x);
+        dd_acc(rs, rc, -vh.y, x.y, -vl.y, xl.y);
+        dd_acc(is, ic, vh.x, x.y, vl.x, xl.y);
+        dd_acc(is, ic, vh.y, x.x, vl.y, xl.x);
+    };
+    // value of entry position p: uniform (index d.z) or explicit (index i)
+    auto val = [&](int4 d, bool uni, int i, auto&& use, int c) {
+        if constexpr (G < 2) {
+            const float vh = uni ? __int_as_float(d.w) : lda(vs + i, pol);
+            const float vl = uni ? __ldg(vsl + d.z) : lda(vsl + i, pol);
+            use(c, vh, vl);
+        } else {
+            const float2 vh = uni ? __ldg(vc + d.z) : lda(vc + i, pol);
+            const float2 vl = uni ? __ldg(vcl + d.z) : lda(vcl + i, pol);
+            use(c, vh, vl);
+        }
+    };
+    auto use = [&](int c, auto vh, auto vl) {
+        if constexpr (G < 2)
+            acc_s(c, vh, vl);
+        else
+            acc_c(c, vh, vl);
+    };
+    if (w <= 0) return;
+    if (type == SELL_G_XU) {
+#pragma unroll 2
+        for (int p = 0; p < w; ++p) {
+            const int4 d = dg(p);
+            val(d, true, 0, use, q ^ d.y);
+        }
+    } else if (type == SELL_G_XE) {
+        const int vb = vbase + dg(0).z + lane;
+#pragma unroll 2
+        for (int p = 0; p < w; ++p) {
+            const int4 d = dg(p);
+            val(d, false, vb + 32 * p, use, q ^ d.y);
+        }
+    } else if (type == SELL_G_EE) {
+        const int4 d0 = dg(0);
+        const int cb = cbase + d0.y + lane, vb = vbase + d0.z + lane;
+#pragma unroll 2
+        for (int p = 0; p < w; ++p) val(d0, false, vb + 32 * p, use, (int)lda(ci + cb + 32 * p, pol));
+    } else {
+        for (int p = 0; p < w; ++p) {
+            const int4 d = dg(p);
+            const int mode = d.x & 3;
+            const int c = mode == SELL_COL_XOR      ? (q ^ d.y)
+                          : mode == SELL_COL_OFFSET ? (q + d.y)
+                                                    : (int)lda(ci + cbase + d.y + lane, pol);
+            const bool uni = (d.x & SELL_VAL_UNIFORM) != 0;
+            val(d, uni, vbase + d.z + lane, use, c);
+        }
+    }
+}
+
+// Row q of A x to about FP64 accuracy in FP32 arithmetic: x = xh + xl (xh
+// gathered like the stage inputs, xl from global memory), A = vh + vl.
+// Returns {re hi, im hi, re lo, im lo} with |lo| <= ulp(hi) / 2.
+template <class IT, bool XS, bool DC>
+__device__ __forceinline__ float4 sell_row_dd(int q, const int4* __restrict__ sl,
+                                              const int4* __restrict__ desc, const SellConst& C,
+                                              const IT* __restrict__ ci, const float* __restrict__ vs,
+                                              const float2* __restrict__ vc, const float* __restrict__ vsl,
+                                              const float2* __restrict__ vcl, const float2* xh,
+                                              const float2* xl, unsigned long long pol) {
+    unsigned xsa = 0;
+    if constexpr (XS) xsa = (unsigned)__cvta_generic_to_shared(xh);
+    auto gx = [&](int c) -> float2 {
+        if constexpr (XS) return lds2(xsa + (unsigned)c * (unsigned)sizeof(float2), float2{});
+        return xh[c];
+    };
+    auto gl = [&](int c) -> float2 { return xl[c]; };
+    const int lane = q & 31;
+    const int4 a = __ldg(sl + 2 * (q >> 5));
+    const int4 b = __ldg(sl + 2 * (q >> 5) + 1);
+    auto dgi = [&](int i) -> int4 {
+        if constexpr (DC)
+            return C.d[i];
+        else
+            return __ldg(desc + i);
+    };
+    const int g1 = a.x + a.y, g2 = g1 + a.z;
+    float rs = 0.f, rc = 0.f, is = 0.f, ic = 0.f;
+    sell_group_dd<0, IT>(q, lane, a.y, b.w & 3, [&](int p) { return dgi(a.x + p); }, b.x, b.y, ci, vs, vc,
+                         vsl, vcl, gx, gl, pol, rs, rc, is, ic);
+    sell_group_dd<1, IT>(q, lane, a.z, (b.w >> 2) & 3, [&](int p) { return dgi(g1 + p); }, b.x, b.y, ci,
+                         vs, vc, vsl, vcl, gx, gl, pol, rs, rc, is, ic);
+    sell_group_dd<2, IT>(q, lane, a.w, (b.w >> 4) & 3, [&](int p) { return dgi(g2 + p); }, b.x, b.z, ci,
+                         vs, vc, vsl, vcl, gx, gl, pol, rs, rc, is, ic);
+    // renormalise: hi = fl(s + c), lo = the exact remainder (Fast2Sum, |s| >= |c|)
+    const float hr = __fadd_rn(rs, rc), hi_ = __fadd_rn(is, ic);
+    return make_float4(hr, hi_, __fsub_rn(rc, __fsub_rn(hr, rs)), __fsub_rn(ic, __fsub_rn(hi_, is)));
+}
+
 template <bool MIXED, class IT, bool XS, bool DC>
 __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_constant__ SellConst C) {
     using T = typename MPrec<MIXED>::T;
@@ -272,6 +422,10 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
     unsigned char* kbase = base + 4 * vb;
     T2* EP = (T2*)(base + 11 * vb);
     float* SC = (float*)(base + 12 * vb);
+    // mixed precision: f (role i) hi and lo parts, and the stage-7 input's remainder
+    auto FHp = [&](int i) -> float2* { return (float2*)(base + (size_t)(2 + i) * vb); };
+    auto FLp = [&](int i) -> float2* { return (float2*)(base + (size_t)(2 + i) * vb) + n; };
+    float2* XL = (float2*)(base + 13 * vb);
     // stage inputs: shared memory (XS; the compiler then addresses them with
     // 32-bit shared loads) or the CTA's scratch
     T2 *X0, *X1;
@@ -280,13 +434,30 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
         X0 = (T2*)xs;
         X1 = J.xbufs > 1 ? (T2*)(xs + (((size_t)n * sizeof(T2) + 15) & ~(size_t)15)) : X0;
     } else {
-        X0 = (T2*)(base + 13 * vb);
-        X1 = (T2*)(base + 14 * vb);
+        X0 = (T2*)(base + 14 * vb);
+        X1 = (T2*)(base + 15 * vb);
     }
     const bool xsingle = X1 == X0;
     const unsigned long long pol = l2_evict_last();
     auto rhs_row = [&](int r, const T2* x) -> T2 {
         return sell_row<MIXED, T, T2, IT, XS, DC>(r, J.sl, J.sdesc, C, (const IT*)J.sci, svs, svc, x, pol);
+    };
+    // mixed precision: f = A (X + XL) for every row into slot `role` (pair)
+    auto base_deriv = [&](int role, const T2* xh) {
+        if constexpr (MIXED) {
+            float2* fh = FHp(role);
+            float2* fl = FLp(role);
+            for (int q = tid; q < n; q += MW_T) {
+                const float4 r = sell_row_dd<IT, XS, DC>(q, J.sl, J.sdesc, C, (const IT*)J.sci, J.svs32,
+                                                         J.svc32, J.svs32lo, J.svc32lo, xh, XL, pol);
+                fh[q] = make_float2(r.x, r.y);
+                fl[q] = make_float2(r.z, r.w);
+            }
+        }
+    };
+    // the FP32 remainder of v after rounding to hi
+    auto lo_of = [](double2 v, float2 hi) {
+        return make_float2((float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y));
     };
 
     long long& acc_steps = z.acc_steps;  // thread 0 only, as all of z
@@ -317,7 +488,11 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
         status = QTL_OK;
     }
 
-    for (int jt = blockIdx.x; jt < J.ntraj; jt += gridDim.x) {
+    // trajectories: the first one per CTA by block index, then the next free
+    // one from a device counter (trajectories differ in length: number of
+    // jumps and steps), so no CTA idles while another still has two to go
+    __shared__ int s_next;
+    for (int jt = blockIdx.x; jt < J.ntraj; jt = s_next) {
         const unsigned long long traj = (unsigned long long)(J.traj_offset + jt);
         int ys = 0;   // Y[ys] = y, Y[ys ^ 1] = y_new (same for YF)
         int k0s = 0;  // slot of k_1: 0 or 6 (k_7 takes the other)
@@ -335,11 +510,15 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
         for (int q = tid; q < n; q += MW_T) {
             const double2 v = J.psi0[q];
             Yp(0)[q] = v;
-            if constexpr (MIXED) YFp(0)[q] = make_float2((float)v.x, (float)v.y);
-            X0[q] = from_d2_mc<T2>(v);
+            const T2 o = from_d2_mc<T2>(v);
+            X0[q] = o;
+            if constexpr (MIXED) XL[q] = lo_of(v, o);
         }
         __syncthreads();
-        for (int q = tid; q < n; q += MW_T) Kp(0)[q] = rhs_row(q, X0);
+        if constexpr (MIXED)
+            base_deriv(0, X0);
+        else
+            for (int q = tid; q < n; q += MW_T) Kp(0)[q] = rhs_row(q, X0);
         __syncthreads();
 
         // <psi|O_e|psi>/<psi|psi> for psi = Y[ys] (written and synchronised by
@@ -411,6 +590,15 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             if (J.n_c == 0) r = 0.0;   // no channel to jump to: never below the threshold
             rhs_evals += 1;
         }
+        // k_1 = f of the current state
+        auto k1_of = [&](int q) -> double2 {
+            if constexpr (MIXED) {
+                const float2 a = FHp(ys)[q], b = FLp(ys)[q];
+                return make_double2((double)a.x + (double)b.x, (double)a.y + (double)b.y);
+            } else {
+                return Kp(0)[q];
+            }
+        };
         // ---- starting step ----
         if (J.fixed) {
             if (tid == 0) h = J.dt_fixed;
@@ -420,7 +608,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             double s0 = 0.0, s1 = 0.0;
             for (int q = tid; q < n; q += MW_T) {
                 const double2 y = Yp(ys)[q];
-                const double2 f0 = to_d2_mc(Kp(0)[q]);
+                const double2 f0 = k1_of(q);
                 const float a = sqrtf((float)(y.x * y.x + y.y * y.y));
                 const float sc = (float)J.atol + (float)J.rtol * a;
                 const float q0 = a / sc, q1 = sqrtf((float)(f0.x * f0.x + f0.y * f0.y)) / sc;
@@ -434,7 +622,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             const double h0 = start_h0(d0, d1);
             for (int q = tid; q < n; q += MW_T) {
                 const double2 y = Yp(ys)[q];
-                const double2 f0 = to_d2_mc(Kp(0)[q]);
+                const double2 f0 = k1_of(q);
                 X1[q] = from_d2_mc<T2>(make_double2(y.x + h0 * f0.x, y.y + h0 * f0.y));
             }
             __syncthreads();
@@ -442,7 +630,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             for (int q = tid; q < n; q += MW_T) {
                 const double2 y = Yp(ys)[q];
                 const double2 f1 = to_d2_mc(rhs_row(q, X1));
-                const double2 f0 = to_d2_mc(Kp(0)[q]);
+                const double2 f0 = k1_of(q);
                 const float sc = (float)J.atol + (float)J.rtol * sqrtf((float)(y.x * y.x + y.y * y.y));
                 const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
                 const float qq = sqrtf(dx * dx + dy * dy) / sc;
@@ -509,6 +697,29 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                     cb.coef[lane] = c;
                     cb.coeff[lane] = (float)c;
                 }
+                if constexpr (MIXED) {
+                    if (lane >= 28) {
+                        // htry^2 W_s for the stages s = 2..5 (0-based) of the increment form
+                        const int st = lane - 26;
+                        double w = 0.0;
+                        for (int l = 0; l < st; ++l) w += tab.a[st][l] * tab.c[l];
+                        cb.c2w[st] = (float)(hh * hh * w);
+                        if (lane == 28) {
+                            cb.hd = hh;
+                            cb.hf = (float)hh;
+                        } else if (lane == 29) {
+                            double bc = 0.0;
+                            for (int j = 0; j < 7; ++j) bc += tab.a[6][j] * tab.c[j];
+                            cb.c2b = hh * hh * bc;
+                        } else if (lane == 30) {
+                            double ec = 0.0;
+                            for (int j = 0; j < 7; ++j) ec += tab.e[j] * tab.c[j];
+                            cb.c2e = (float)(hh * hh * ec);
+                        } else {
+                            cb.he7h = (float)(hh * tab.e[6] * hh);
+                        }
+                    }
+                }
             }
             __syncwarp();
         };
@@ -517,6 +728,103 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
         // (scaled, summed in FP32 as in the register-resident kernel) and
         // |y_new|^2 (FP64); both are left as thread partials in *se, *sn.
         auto rk_step = [&](float* se_out, double* sn_out) {
+          if constexpr (MIXED) {
+            float se = 0.f;
+            double sn = 0.0;
+            const double2* y = Yp(ys);
+            double2* yn = Yp(ys ^ 1);
+            const float2* fh = FHp(ys);
+            const float2* fl = FLp(ys);
+            float2* fnh = FHp(ys ^ 1);
+            float2* fnl = FLp(ys ^ 1);
+            const float2* f2 = (const float2*)Kp(1);
+#pragma unroll 1
+            for (int s = 1; s < 7; ++s) {
+                float2* xb = (float2*)((s & 1) ? X0 : X1);
+                if (s == 1) {
+                    // stage 2 evaluates f2 = A f
+#pragma unroll 2
+                    for (int q = tid; q < n; q += MW_T) xb[q] = __ldcs(fh + q);
+                } else if (s < 6) {
+                    // d_s = h^2 W_s f2 + sum_{2 <= l < s} h a_sl r_l
+                    const int ca = mc_coef_a(s, 0);
+                    const float w = cb.c2w[s];
+#pragma unroll 2
+                    for (int q = tid; q < n; q += MW_T) {
+                        const float2 g = __ldcs(f2 + q);
+                        float ax = w * g.x, ay = w * g.y;
+#pragma unroll
+                        for (int j = 2; j < 5; ++j) {
+                            if (j < s) {
+                                const float2 kv = __ldcs((const float2*)Kp(j) + q);
+                                const float a = cb.coeff[ca + j];
+                                ax = fmaf(a, kv.x, ax);
+                                ay = fmaf(a, kv.y, ay);
+                            }
+                        }
+                        xb[q] = make_float2(ax, ay);
+                    }
+                } else {
+                    // y_new = y + h f + h^2 (sum b c) f2 + sum_j h b_j r_j in FP64;
+                    // the error partial h^2 (sum e c) f2 + sum_{j<7} h e_j r_j
+                    // - h e_7 (f + h f2), completed by + h e_7 f_new below
+                    const int ca = mc_coef_a(6, 0);
+                    const double hd = cb.hd, c2b = cb.c2b;
+                    const float hf = cb.hf, c2e = cb.c2e, he7 = cb.coeff[27], he7h = cb.he7h;
+#pragma unroll 2
+                    for (int q = tid; q < n; q += MW_T) {
+                        const float2 g = __ldcs(f2 + q);
+                        const float2 fa = __ldcs(fh + q), fb = __ldcs(fl + q);
+                        float rx = hf * fb.x, ry = hf * fb.y;
+                        float ex = fmaf(c2e, g.x, fmaf(-he7h, g.x, -he7 * (fa.x + fb.x)));
+                        float ey = fmaf(c2e, g.y, fmaf(-he7h, g.y, -he7 * (fa.y + fb.y)));
+#pragma unroll
+                        for (int j = 2; j < 6; ++j) {
+                            const float2 kv = __ldcs((const float2*)Kp(j) + q);
+                            const float b = cb.coeff[ca + j], e = cb.coeff[21 + j];
+                            rx = fmaf(b, kv.x, rx);
+                            ry = fmaf(b, kv.y, ry);
+                            ex = fmaf(e, kv.x, ex);
+                            ey = fmaf(e, kv.y, ey);
+                        }
+                        const double2 yv = __ldcs(y + q);
+                        const double2 nv = make_double2(fma(c2b, (double)g.x, fma(hd, (double)fa.x, yv.x)) + (double)rx,
+                                                        fma(c2b, (double)g.y, fma(hd, (double)fa.y, yv.y)) + (double)ry);
+                        __stcs(yn + q, nv);
+                        const float2 o = make_float2((float)nv.x, (float)nv.y);
+                        XL[q] = lo_of(nv, o);
+                        const float yx = (float)yv.x, yy = (float)yv.y;
+                        const float a2 = fmaxf(yx * yx + yy * yy, o.x * o.x + o.y * o.y);
+                        __stcs(SC + q, (float)J.atol + (float)J.rtol * sqrtf(a2));
+                        __stcs((float2*)EP + q, make_float2(ex, ey));
+                        sn += nv.x * nv.x + nv.y * nv.y;
+                        xb[q] = o;
+                    }
+                }
+                __syncthreads();
+                if (s < 6) {
+                    T2* ks = Kp(s);
+#pragma unroll 2
+                    for (int q = tid; q < n; q += MW_T) __stcs(ks + q, rhs_row(q, (const T2*)xb));
+                } else {
+                    // f_new = A y_new, error free; completes the error estimate
+                    const float he7 = cb.coeff[27];
+                    for (int q = tid; q < n; q += MW_T) {
+                        const float4 r = sell_row_dd<IT, XS, DC>(q, J.sl, J.sdesc, C, (const IT*)J.sci, J.svs32,
+                                                                 J.svc32, J.svs32lo, J.svc32lo, xb, XL, pol);
+                        __stcs(fnh + q, make_float2(r.x, r.y));
+                        __stcs(fnl + q, make_float2(r.z, r.w));
+                        const float2 ep = __ldcs((const float2*)EP + q);
+                        const float fx = fmaf(he7, r.x, ep.x), fy = fmaf(he7, r.y, ep.y);
+                        const float sc = __ldcs(SC + q);
+                        se += (fx * fx + fy * fy) / (sc * sc);
+                    }
+                }
+                if (xsingle) __syncthreads();
+            }
+            *se_out = se;
+            *sn_out = sn;
+          } else {
             float se = 0.f;
             double sn = 0.0;
             const double2* y = Yp(ys);
@@ -617,6 +925,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             }
             *se_out = se;
             *sn_out = sn;
+          }
         };
         // FP32 error sum and FP64 |y_new|^2, warps -> thread 0.
         auto reduce_step = [&](float se, double sn, float* S, double* N) {
@@ -817,13 +1126,15 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                     const double2 nv = make_double2(vx * inv, vy * inv);
                     Yp(ys)[q] = nv;
                     const T2 o = from_d2_mc<T2>(nv);
-                    if constexpr (MIXED) YFp(ys)[q] = o;
+                    if constexpr (MIXED) XL[q] = lo_of(nv, o);
                     X0[q] = o;
                     n2p += nv.x * nv.x + nv.y * nv.y;
                 }
             }
             __syncthreads();
-            {
+            if constexpr (MIXED) {
+                base_deriv(ys, X0);
+            } else {
                 T2* k0 = Kp(0);
                 for (int q = tid; q < n; q += MW_T) k0[q] = rhs_row(q, X0);
             }
@@ -835,6 +1146,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             }
             __syncthreads();
         }
+        if (tid == 0) s_next = J.wnext ? (int)gridDim.x + atomicAdd(J.wnext, 1) : jt + (int)gridDim.x;
         __syncthreads();
     }
     if (tid == 0) {

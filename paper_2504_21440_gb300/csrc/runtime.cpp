@@ -296,6 +296,10 @@ static void free_csr(DevCsr& d) {
     d = DevCsr();
 }
 
+qtl_status op_to_csr(const qtl_op* op, int n_expect, Csr& out) { return to_csr(op, n_expect, out); }
+qtl_status csr_upload(const Csr& m, DevCsr& d) { return upload_csr(m, d); }
+void csr_free(DevCsr& d) { free_csr(d); }
+
 // A in pattern-compressed sliced ELLPACK (see DevSell); entries grouped and
 // ordered as in upload_csr.  Descriptor lists and uniform values are
 // deduplicated across slices.
@@ -483,6 +487,11 @@ static qtl_status upload_sell(const Csr& m, DevSell& d) {
     std::vector<float2> vc32(vc.size());
     for (size_t i = 0; i < vs.size(); ++i) vs32[i] = (float)vs[i];
     for (size_t i = 0; i < vc.size(); ++i) vc32[i] = make_float2((float)vc[i].x, (float)vc[i].y);
+    std::vector<float> vs32lo(vs.size());
+    std::vector<float2> vc32lo(vc.size());
+    for (size_t i = 0; i < vs.size(); ++i) vs32lo[i] = (float)(vs[i] - (double)vs32[i]);
+    for (size_t i = 0; i < vc.size(); ++i)
+        vc32lo[i] = make_float2((float)(vc[i].x - (double)vc32[i].x), (float)(vc[i].y - (double)vc32[i].y));
     d.n = n;
     d.nslices = ns_;
     d.ndesc = (int64_t)desc.size();
@@ -509,6 +518,8 @@ static qtl_status upload_sell(const Csr& m, DevSell& d) {
     if ((st = upload(&d.vs32, vs32.data(), vs32.size())) != QTL_OK) return st;
     if ((st = upload(&d.vc64, vc.data(), vc.size())) != QTL_OK) return st;
     if ((st = upload(&d.vc32, vc32.data(), vc32.size())) != QTL_OK) return st;
+    if ((st = upload(&d.vs32lo, vs32lo.data(), vs32lo.size())) != QTL_OK) return st;
+    if ((st = upload(&d.vc32lo, vc32lo.data(), vc32lo.size())) != QTL_OK) return st;
     return QTL_OK;
 }
 
@@ -520,6 +531,8 @@ static void free_sell(DevSell& d) {
     cudaFree(d.vs32);
     cudaFree(d.vc64);
     cudaFree(d.vc32);
+    cudaFree(d.vs32lo);
+    cudaFree(d.vc32lo);
     d = DevSell();
 }
 
@@ -697,7 +710,15 @@ static qtl_status check_opts(const qtl_opts* o) {
     if (!(o->dt0 >= 0.0) || !(o->dt_min >= 0.0) || o->max_steps <= 0) return QTL_EINVAL;
     if (o->cluster_size < 0 || o->cluster_size > 16) return QTL_EINVAL;
     if (o->engine < QTL_ENGINE_AUTO || o->engine > QTL_ENGINE_GRID) return QTL_EINVAL;
+    if (o->shadow_fp64 != 0 && o->shadow_fp64 != 1) return QTL_EINVAL;
     return QTL_OK;
+}
+
+// max |a_i - b_i| over m complex values
+static double max_abs_diff(const qtl_c128* a, const qtl_c128* b, size_t m) {
+    double e = 0.0;
+    for (size_t i = 0; i < m; ++i) e = std::max(e, std::hypot(a[i].re - b[i].re, a[i].im - b[i].im));
+    return e;
 }
 
 qtl_status validate_opts(const qtl_opts* o) { return check_opts(o); }
@@ -899,7 +920,7 @@ void qtl_opts_default(qtl_opts* o) {
     o->dt_fixed = 0.0;
     o->cuda_stream = nullptr;
     o->engine = QTL_ENGINE_AUTO;
-    o->reserved = 0;
+    o->shadow_fp64 = 0;
 }
 
 const char* qtl_strerror(qtl_status s) {
@@ -936,6 +957,7 @@ void qtl_system_free(qtl_system* sys) {
     cudaFree(s.units);
     cudaFree(s.odiag);
     cudaFree(s.ew);
+    ss_cache_free(s);
     delete sys;
 }
 
@@ -1525,6 +1547,7 @@ extern "C" qtl_status qtl_mesolve_batch(qtl_system* const* systems, int32_t nb,
             stats[b].steps_rej = info[b].steps_rej;
             stats[b].rhs_evals = info[b].rhs_evals;
             stats[b].jumps = info[b].jumps;
+            stats[b].err_vs_fp64 = opts->precision == QTL_FP64 ? 0.0 : -1.0;
         }
         if (first_bad == QTL_OK && info[b].status != QTL_OK) first_bad = (qtl_status)info[b].status;
     }
@@ -1586,6 +1609,17 @@ qtl_status qtl_mesolve(qtl_system* sys, const qtl_c128* state0, int32_t is_ket, 
         stats->steps_rej = info.steps_rej;
         stats->rhs_evals = info.rhs_evals;
         stats->jumps = info.jumps;
+        stats->err_vs_fp64 = opts->precision == QTL_FP64 ? 0.0 : -1.0;
+    }
+    if (info.status == QTL_OK && opts->precision == QTL_MIXED && opts->shadow_fp64 && stats) {
+        // the same solve in FP64, compared on the host
+        qtl_opts o = *opts;
+        o.precision = QTL_FP64;
+        o.shadow_fp64 = 0;
+        std::vector<qtl_c128> ref(ne > 0 ? ne : 1);
+        qtl_stats rs{};
+        if (qtl_mesolve(sys, state0, is_ket, tlist, nt, &o, ref.data(), nullptr, &rs) == QTL_OK)
+            stats->err_vs_fp64 = max_abs_diff(expect_out, ref.data(), ne);
     }
     return (qtl_status)info.status;
 }
@@ -1673,6 +1707,8 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
         J.svs32 = s.sA.vs32;
         J.svc64 = s.sA.vc64;
         J.svc32 = s.sA.vc32;
+        J.svs32lo = s.sA.vs32lo;
+        J.svc32lo = s.sA.vc32lo;
         McWidePlan plan;
         void* wscr = nullptr;
         e = mc_wide_plan(J, opts->precision, &plan);
@@ -1742,6 +1778,17 @@ qtl_status qtl_mcsolve(qtl_system* sys, const qtl_c128* psi0, const double* tlis
         stats->steps_rej = info.steps_rej;
         stats->rhs_evals = info.rhs_evals;
         stats->jumps = info.jumps;
+        stats->err_vs_fp64 = opts->precision == QTL_FP64 ? 0.0 : -1.0;
+    }
+    if (info.status == QTL_OK && opts->precision == QTL_MIXED && opts->shadow_fp64 && stats) {
+        // the same trajectories (same seed and offset) in FP64
+        qtl_opts o = *opts;
+        o.precision = QTL_FP64;
+        o.shadow_fp64 = 0;
+        std::vector<qtl_c128> ref(ne > 0 ? ne : 1);
+        qtl_stats rs{};
+        if (qtl_mcsolve(sys, psi0, tlist, nt, ntraj, seed, traj_offset, &o, ref.data(), nullptr, &rs) == QTL_OK)
+            stats->err_vs_fp64 = max_abs_diff(expect_out, ref.data(), ne);
     }
     return (qtl_status)info.status;
 }

@@ -10,7 +10,9 @@
 // event has completed (copy from staging to the caller's buffer, release of
 // the budget and the slot).  Submit / poll / wait / cancel only touch the
 // queue under a mutex.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -66,7 +68,23 @@ namespace qtl {
 
 // Device bytes a request will hold while it runs (inputs, outputs and the
 // solver's scratch), used for admission.
+static size_t request_bytes_one(const qtl_request& r);
+static bool wants_shadow(const qtl_request& r) {
+    return r.opts.precision == QTL_MIXED && r.opts.shadow_fp64;
+}
+// With the FP64 shadow both solves' buffers are counted: the shadow runs
+// after the reduced-precision solve on the same stream.
 static size_t request_bytes(const qtl_request& r) {
+    size_t b = request_bytes_one(r);
+    if (wants_shadow(r)) {
+        qtl_request f = r;
+        f.opts.precision = QTL_FP64;
+        b += request_bytes_one(f);
+    }
+    return b;
+}
+
+static size_t request_bytes_one(const qtl_request& r) {
     const System& s = r.sys->s;
     const size_t n = (size_t)s.n, L = n * n, nt = (size_t)r.nt, ne = (size_t)(s.n_e > 0 ? s.n_e : 1);
     const size_t t2 = r.opts.precision == QTL_MIXED ? 8 : 16;
@@ -98,7 +116,10 @@ static void srv_admit(qtl_server* S, SrvReq* q, int slot) {
     const size_t n = (size_t)s.n, nt = (size_t)q->r.nt;
     const size_t n0 = (q->r.kind == QTL_REQ_MCSOLVE || q->r.is_ket) ? n : n * n;
     q->ex_bytes = (size_t)s.n_e * nt * 16;
-    const size_t need_pinned = 64 + q->ex_bytes;
+    const bool shadow = wants_shadow(q->r);
+    // pinned staging: [info | expect] and, with the shadow, [info | expect] of the FP64 solve
+    const size_t stage_b = 64 + ((q->ex_bytes + 63) & ~(size_t)63);
+    const size_t need_pinned = shadow ? 2 * stage_b : stage_b;
     q->slot = slot;
     q->state = 1;
     q->res.t_start = now_s();
@@ -114,7 +135,8 @@ static void srv_admit(qtl_server* S, SrvReq* q, int slot) {
     char* dbuf = nullptr;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t o_st = 0, o_tl = up(n0 * 16), o_ex = o_tl + up(nt * 8), o_inf = o_ex + up(q->ex_bytes + 16);
-    const size_t total = o_inf + 256;
+    const size_t o_ex2 = o_inf + 256, o_inf2 = o_ex2 + up(q->ex_bytes + 16);
+    const size_t total = shadow ? o_inf2 + 256 : o_inf + 256;
     if (stt == QTL_OK && qtl_malloc_async((void**)&dbuf, total, st) != cudaSuccess) stt = QTL_ENOMEM;
     if (stt == QTL_OK) {
         cudaMemcpyAsync(dbuf + o_st, q->r.state0, n0 * 16, cudaMemcpyHostToDevice, st);
@@ -134,6 +156,32 @@ static void srv_admit(qtl_server* S, SrvReq* q, int slot) {
             cudaMemcpyAsync(sl.pinned, dinfo, sizeof(qtl_device_info), cudaMemcpyDeviceToHost, st);
             if (q->ex_bytes)
                 cudaMemcpyAsync((char*)sl.pinned + 64, dbuf + o_ex, q->ex_bytes, cudaMemcpyDeviceToHost, st);
+        }
+        if (stt == QTL_OK && shadow) {
+            // the same request in FP64, after the reduced-precision solve
+            qtl_opts f = o;
+            f.precision = QTL_FP64;
+            f.shadow_fp64 = 0;
+            qtl_device_info* dinfo2 = (qtl_device_info*)(dbuf + o_inf2);
+            qtl_status s2;
+            if (q->r.kind == QTL_REQ_MESOLVE)
+                s2 = qtl_mesolve_async(q->r.sys, (const qtl_c128*)(dbuf + o_st), q->r.is_ket,
+                                       (const double*)(dbuf + o_tl), q->r.nt, &f,
+                                       (qtl_c128*)(dbuf + o_ex2), nullptr, dinfo2);
+            else
+                s2 = qtl_mcsolve_async(q->r.sys, (const qtl_c128*)(dbuf + o_st),
+                                       (const double*)(dbuf + o_tl), q->r.nt, q->r.ntraj, q->r.seed, 0,
+                                       &f, (qtl_c128*)(dbuf + o_ex2), nullptr, dinfo2);
+            char* p2 = (char*)sl.pinned + stage_b;
+            if (s2 == QTL_OK) {
+                cudaMemcpyAsync(p2, dinfo2, sizeof(qtl_device_info), cudaMemcpyDeviceToHost, st);
+                if (q->ex_bytes)
+                    cudaMemcpyAsync(p2 + 64, dbuf + o_ex2, q->ex_bytes, cudaMemcpyDeviceToHost, st);
+            } else {
+                qtl_device_info fail{};
+                fail.status = s2;
+                std::memcpy(p2, &fail, sizeof(fail));
+            }
         }
         cudaFreeAsync(dbuf, st);
     }
@@ -157,8 +205,23 @@ static void srv_retire(qtl_server* S, int slot) {
     q->res.stats.steps_rej = info.steps_rej;
     q->res.stats.rhs_evals = info.rhs_evals;
     q->res.stats.jumps = info.jumps;
+    q->res.stats.err_vs_fp64 = q->r.opts.precision == QTL_FP64 ? 0.0 : -1.0;
     if (q->ex_bytes && q->res.status == QTL_OK && q->expect_out)
         std::memcpy(q->expect_out, (char*)sl.pinned + 64, q->ex_bytes);
+    if (q->res.status == QTL_OK && wants_shadow(q->r) && sl.pinned) {
+        const size_t stage_b = 64 + ((q->ex_bytes + 63) & ~(size_t)63);
+        const char* p2 = (const char*)sl.pinned + stage_b;
+        qtl_device_info info2{};
+        std::memcpy(&info2, p2, sizeof(info2));
+        if (info2.status == QTL_OK) {
+            const qtl_c128* a = (const qtl_c128*)((const char*)sl.pinned + 64);
+            const qtl_c128* b = (const qtl_c128*)(p2 + 64);
+            double e = 0.0;
+            for (size_t i = 0; i < q->ex_bytes / 16; ++i)
+                e = std::max(e, std::hypot(a[i].re - b[i].re, a[i].im - b[i].im));
+            q->res.stats.err_vs_fp64 = e;
+        }
+    }
     q->res.t_end = now_s();
     q->state = 2;
     sl.req = nullptr;

@@ -37,15 +37,17 @@ class Opts(C.Structure):
                 ("atol", C.c_double), ("dt0", C.c_double), ("dt_min", C.c_double),
                 ("max_steps", C.c_int64), ("fixed_step", C.c_int32), ("cluster_size", C.c_int32),
                 ("dt_fixed", C.c_double), ("cuda_stream", C.c_void_p), ("engine", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("shadow_fp64", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("steps_acc", C.c_int64), ("steps_rej", C.c_int64), ("rhs_evals", C.c_int64),
-                ("jumps", C.c_int64)]
+                ("jumps", C.c_int64), ("err_vs_fp64", C.c_double)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:4]}
+        d["err_vs_fp64"] = float(self.err_vs_fp64)
+        return d
 
 
 class Request(C.Structure):
@@ -57,6 +59,20 @@ class Request(C.Structure):
 class Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("stats", Stats), ("t_submit", C.c_double),
                 ("t_start", C.c_double), ("t_end", C.c_double)]
+
+
+class SsOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class SsStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("pad", C.c_int32), ("residual", C.c_double),
+                ("cond_v", C.c_double), ("gmres_residual", C.c_double)]
+
+    def as_dict(self):
+        return dict(iterations=int(self.iterations), residual=float(self.residual),
+                    cond_v=float(self.cond_v), gmres_residual=float(self.gmres_residual))
 
 
 class DeviceInfo(C.Structure):
@@ -133,6 +149,13 @@ def load():
                                         C.c_int32, P, P, P, P, P, C.c_int32, C.c_int32,
                                         C.c_uint64, C.c_int64, C.POINTER(Opts), P, P]
     lib.qtl_mcsolve_noalloc.restype = C.c_int
+    lib.qtl_ss_opts_default.argtypes = [C.POINTER(SsOpts)]
+    lib.qtl_ss_opts_default.restype = None
+    lib.qtl_steadystate.argtypes = [P, C.POINTER(SsOpts), P, C.POINTER(SsStats)]
+    lib.qtl_steadystate.restype = C.c_int
+    lib.qtl_steadystate_fourier.argtypes = [P, C.POINTER(Op), C.c_double, C.c_double, C.c_int32,
+                                            C.POINTER(SsOpts), P, C.POINTER(SsStats)]
+    lib.qtl_steadystate_fourier.restype = C.c_int
     lib.qtl_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(P)]
     lib.qtl_server_create.restype = C.c_int
     lib.qtl_server_submit.argtypes = [P, C.POINTER(Request), P, C.POINTER(C.c_uint64)]
@@ -176,7 +199,8 @@ def opts_default():
 
 
 def make_opts(method="tsit5", precision="fp64", rtol=1e-8, atol=1e-10, dt0=0.0, dt_min=0.0,
-              max_steps=10_000_000, fixed_dt=None, cluster_size=0, stream=None, engine="auto"):
+              max_steps=10_000_000, fixed_dt=None, cluster_size=0, stream=None, engine="auto",
+              shadow_fp64=False):
     o = opts_default()
     o.method = METHODS[method]
     o.precision = PRECISIONS[precision]
@@ -187,6 +211,7 @@ def make_opts(method="tsit5", precision="fp64", rtol=1e-8, atol=1e-10, dt0=0.0, 
     o.cluster_size = int(cluster_size)
     o.cuda_stream = stream
     o.engine = ENGINES[engine]
+    o.shadow_fp64 = 1 if shadow_fp64 else 0
     return o
 
 
@@ -533,6 +558,36 @@ def mcsolve_noalloc(n, a_csr, c_csr, n_c, o_csr, n_e, psi0_dev, tlist_dev, ntraj
            "qtl_mcsolve_noalloc")
 
 
+def ss_opts(tol=1e-12, restart=60, max_iter=20000, stream=None):
+    o = SsOpts()
+    load().qtl_ss_opts_default(C.byref(o))
+    o.tol, o.restart, o.max_iter, o.cuda_stream = float(tol), int(restart), int(max_iter), stream
+    return o
+
+
+def steadystate(sys, opts):
+    """qtl_steadystate: returns dict(rho (n x n), stats)."""
+    n = system_dim(sys)
+    out = np.zeros(n * n, dtype=np.complex128)
+    st = SsStats()
+    _check(load().qtl_steadystate(sys, C.byref(opts), _ptr(out), C.byref(st)), "qtl_steadystate")
+    return dict(rho=out.reshape((n, n), order="F"), stats=st.as_dict())
+
+
+def steadystate_fourier(sys, X, F, omega, nmax, opts):
+    """qtl_steadystate_fourier: returns dict(rho = {k: rho_k}, stats)."""
+    n = system_dim(sys)
+    K = 2 * int(nmax) + 1
+    out = np.zeros(K * n * n, dtype=np.complex128)
+    st = SsStats()
+    xo = _OpHolder(X)
+    _check(load().qtl_steadystate_fourier(sys, C.byref(xo.op), float(F), float(omega), int(nmax),
+                                          C.byref(opts), _ptr(out), C.byref(st)),
+           "qtl_steadystate_fourier")
+    rho = {a - int(nmax): out[a * n * n:(a + 1) * n * n].reshape((n, n), order="F") for a in range(K)}
+    return dict(rho=rho, stats=st.as_dict())
+
+
 class System:
     """Owning wrapper: System(H, c_ops, e_ops) -> .mesolve(...) / .mcsolve(...)."""
 
@@ -562,6 +617,12 @@ class System:
 
     def sesolve(self, psi0, tlist, **kw):
         return sesolve(self.handle, self.n_e, psi0, tlist, make_opts(**kw))
+
+    def steadystate(self, **kw):
+        return steadystate(self.handle, ss_opts(**kw))
+
+    def steadystate_fourier(self, X, F, omega, nmax, **kw):
+        return steadystate_fourier(self.handle, X, F, omega, nmax, ss_opts(**kw))
 
     def mcsolve(self, psi0, tlist, ntraj, seed, traj_offset=0, keep_trajectories=False, **kw):
         return mcsolve(self.handle, self.n_e, psi0, tlist, ntraj, seed, make_opts(**kw),

@@ -64,20 +64,24 @@ def test_wide_int32_columns_ising17():
     s = W.ising_chain(17, gamma=0.5, t_end=0.3, nt=4)
     ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=3, seed=21,
                          fixed_dt=0.01, keep_trajectories=True)
-    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-6)):
         got = _gpu(s, s.tlist, 3, 21, fixed_dt=0.01, precision=prec)
         assert got["stats"]["jumps"] == ref["stats"]["jumps"] > 0
         assert maxabs(got["traj_expect"], ref["traj_expect"]) <= tol
 
 
+MIXED = dict(precision="mixed", rtol=1e-7, atol=1e-9)
+
+
 def test_wide_mixed_precision_ising11():
+    """Mixed-precision trajectories against the oracle run at the same
+    tolerances, trajectory by trajectory, at the 1e-6 bar."""
     s = W.ising_chain(11, t_end=4.0, nt=21)
     ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=8, seed=3,
-                         keep_trajectories=True)
-    got = _gpu(s, s.tlist, 8, 3, precision="mixed", rtol=1e-7, atol=1e-9)
-    close = [j for j in range(8)
-             if maxabs(got["traj_expect"][j], ref["traj_expect"][j]) <= 1e-5]
-    assert len(close) >= 7
+                         rtol=1e-7, atol=1e-9, keep_trajectories=True)
+    got = _gpu(s, s.tlist, 8, 3, **MIXED)
+    assert got["stats"]["jumps"] == ref["stats"]["jumps"] > 0
+    assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-6
 
 
 def test_wide_edge_cases():
@@ -105,11 +109,15 @@ def test_ising14_full_size_sampled():
     the same two trajectories (traj_offset selects their streams)."""
     s = W.ising_chain(14, t_end=2.0, nt=21)
     ids = [0, 1999]
+    # the oracle at the mixed solve's tolerances (rtol 1e-7), and at the FP64
+    # defaults (rtol 1e-8) for the FP64 kernel
+    ref7 = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=len(ids), seed=9,
+                          traj_ids=ids, rtol=1e-7, atol=1e-9, keep_trajectories=True)
     ref = oracle_mcsolve(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, ntraj=len(ids), seed=9,
                          traj_ids=ids, keep_trajectories=True)
-    mixed = _gpu(s, s.tlist, 2000, 9, precision="mixed", rtol=1e-7, atol=1e-9)
+    mixed = _gpu(s, s.tlist, 2000, 9, **MIXED)
     for i, j in enumerate(ids):
-        assert maxabs(mixed["traj_expect"][j], ref["traj_expect"][i]) <= 1e-5
+        assert maxabs(mixed["traj_expect"][j], ref7["traj_expect"][i]) <= 1e-6
     # ensemble: Sz decays from 14; |Sx|, |Sy| <= 14 on every trajectory
     per = mixed["traj_expect"]
     assert np.all(np.abs(per.real) <= 14 + 1e-6)
@@ -117,3 +125,49 @@ def test_ising14_full_size_sampled():
     for i, j in enumerate(ids):
         f = _gpu(s, s.tlist, 1, 9, traj_offset=j)
         assert maxabs(f["traj_expect"][0], ref["traj_expect"][i]) <= 1e-8
+
+
+def test_ising14_full_span_mixed_within_1e6_of_fp64():
+    """The benchmark's 14-spin solve over its whole span (t in [0, 10], 100
+    output times, seed 3), 152 trajectories (one per SM), mixed precision
+    against the FP64 kernel with the same draws (itself checked against the
+    oracle above).
+    - Fixed steps of 0.0125 (the adaptive solve's typical step): both sides
+      take the same steps, so the difference is the arithmetic alone; every
+      trajectory and every Sx, Sy, Sz value is within 1e-6.
+    - Adaptive (rtol 1e-7): the reported ensemble means are within 1e-6,
+      and the library's err_vs_fp64 is that difference.  Single adaptive
+      trajectories are not compared at 1e-6: two solves at rtol 1e-7 that
+      take different steps already differ by the truncation error (FP64 at
+      rtol 1e-7 against FP64 at rtol 1e-9: 1.4e-6 on Sz)."""
+    qtl = require_gpu()
+    s = W.ising_chain(14)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    try:
+        fm = g.mcsolve(s.psi0, s.tlist, 152, 3, keep_trajectories=True, precision="mixed", fixed_dt=0.0125)
+        ff = g.mcsolve(s.psi0, s.tlist, 152, 3, keep_trajectories=True, precision="fp64", fixed_dt=0.0125)
+        m = g.mcsolve(s.psi0, s.tlist, 152, 3, **MIXED)
+        f = g.mcsolve(s.psi0, s.tlist, 152, 3, **dict(MIXED, precision="fp64"))
+        sh = g.mcsolve(s.psi0, s.tlist, 152, 3, shadow_fp64=True, **MIXED)
+    finally:
+        g.free()
+    assert fm["stats"]["jumps"] == ff["stats"]["jumps"] > 0
+    assert maxabs(fm["traj_expect"], ff["traj_expect"]) <= 1e-6
+    assert maxabs(m["expect"], f["expect"]) <= 1e-6
+    assert sh["stats"]["err_vs_fp64"] == maxabs(m["expect"], f["expect"])
+
+
+def test_ising14_mixed_ensemble_within_sampling_error_of_fp64():
+    """600 trajectories of the 14-spin chain: the mixed ensemble mean is
+    within 3 sigma / sqrt(ntraj) of the FP64 ensemble at every time."""
+    qtl = require_gpu()
+    s = W.ising_chain(14)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    try:
+        m = g.mcsolve(s.psi0, s.tlist, 600, 5, **MIXED)
+        f = g.mcsolve(s.psi0, s.tlist, 600, 5, keep_trajectories=True, **dict(MIXED, precision="fp64"))
+    finally:
+        g.free()
+    sd = f["traj_expect"].real.std(axis=0)
+    bound = 3 * np.maximum(sd, 1e-3) / math.sqrt(600) + 1e-6
+    assert np.all(np.abs(m["expect"].real - f["expect"].real) <= bound)

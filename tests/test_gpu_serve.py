@@ -68,3 +68,45 @@ def test_budget_refusal_and_cancel():
         assert r2["status"] == 0
     srv.free()
     g.free()
+
+
+def test_served_mixed_results_against_fp64_and_the_oracle():
+    """Requests drawn from the serving mix (coupled-cavity mesolve and Ising
+    mcsolve, mixed precision, each with its FP64 shadow): every mesolve
+    result is within 1e-6 of the FP64 oracle, and of the FP64 solve the
+    server ran beside it (err_vs_fp64); every mcsolve result is within
+    3 sigma / sqrt(ntraj) of the FP64 ensemble with the same random draws,
+    and its reported err_vs_fp64 is that difference."""
+    from oracle.mesolve import mesolve as o_me
+    qtl = require_gpu()
+    mix = W.serving_mix(n_requests=12, seed=5, rate=1000.0, ising_spins=(5, 7),
+                        ntraj=(100, 200), cav=(4, 9))
+    systems = [qtl.System(r["system"].H, r["system"].c_ops, r["system"].e_ops) for r in mix]
+    srv = qtl.Server(max_inflight=8)
+    opts = qtl.make_opts(shadow_fp64=True, **dict(precision="mixed", rtol=1e-7, atol=1e-9))
+    tickets = [srv.submit(r["kind"], g, r["system"].psi0, r["system"].tlist, opts,
+                          ntraj=r.get("ntraj", 0), seed=r.get("seed", 0))
+               for r, g in zip(mix, systems)]
+    results = [srv.wait(t) for t in tickets]
+    srv.free()
+    kinds = set()
+    for r, g, res in zip(mix, systems, results):
+        s = r["system"]
+        assert res["status"] == 0
+        err = res["stats"]["err_vs_fp64"]
+        assert err >= 0.0
+        kinds.add(r["kind"])
+        if r["kind"] == "mesolve":
+            ref = o_me(s.H, s.c_ops, s.e_ops, s.psi0, s.tlist, rtol=1e-8, atol=1e-10)
+            assert maxabs(res["expect"], ref["expect"]) <= 1e-6
+            assert err <= 1e-6
+        else:
+            f = g.mcsolve(s.psi0, s.tlist, r["ntraj"], r["seed"], keep_trajectories=True,
+                          precision="fp64", rtol=1e-7, atol=1e-9)
+            assert err == maxabs(res["expect"], f["expect"])
+            sd = f["traj_expect"].real.std(axis=0)
+            bound = 3 * np.maximum(sd, 1e-3) / np.sqrt(r["ntraj"]) + 1e-6
+            assert np.all(np.abs(res["expect"].real - f["expect"].real) <= bound)
+    assert kinds == {"mesolve", "mcsolve"}
+    for g in systems:
+        g.free()
