@@ -282,12 +282,16 @@ qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlis
  *   expect_out[n_e*nt]: trajectory mean of <psi|O_k|psi>/<psi|psi>;
  *   meas_out[n_c*nt]:   trajectory mean of J_n of the last step ending at or
  *                       before each time (e_n(psi0) at tlist[0]).
+ *   traj_expect_out, traj_meas_out: NULL, or the per-trajectory values,
+ *                       [n_e*nt*ntraj] and [n_c*nt*ntraj] laid out
+ *                       [(k*nt + t)*ntraj + j] as for qtl_mcsolve.
  * Host pointers; returns when done; stats->steps_acc = steps over all
  * trajectories.  QTL_ESTEP, before any work, when (tlist[nt-1] - tlist[0]) /
  * dt_fixed exceeds opts->max_steps (a trajectory's step count). */
 qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt,
                         int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
-                        double* meas_out, qtl_stats* stats);
+                        double* meas_out, qtl_stats* stats, qtl_c128* traj_expect_out,
+                        double* traj_meas_out);
 
 /* smesolve (Sec. 3.5): the stochastic master equation under homodyne
  * detection, in Ito form
@@ -302,10 +306,12 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
  * opts->dt_fixed, FP64, the same Wiener increments and step budget), without
  * renormalisation (the scheme keeps Tr rho = 1 up to rounding).
  *   expect_out[n_e*nt]: trajectory mean of Tr(O_k rho);
- *   meas_out[n_sc*nt]:  trajectory mean of J_n, recorded as in qtl_ssesolve. */
+ *   meas_out[n_sc*nt]:  trajectory mean of J_n, recorded as in qtl_ssesolve;
+ *   traj_expect_out, traj_meas_out: NULL or per trajectory, as in qtl_ssesolve. */
 qtl_status qtl_smesolve(qtl_system* sys, int32_t n_sc, const qtl_c128* psi0, const double* tlist, int32_t nt,
                         int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out,
-                        double* meas_out, qtl_stats* stats);
+                        double* meas_out, qtl_stats* stats, qtl_c128* traj_expect_out,
+                        double* traj_meas_out);
 
 /* Reusable batch plan (Sec. 3.2 over nb independent systems, as
  * qtl_mesolve_batch_async), built once and replayed.

@@ -1091,7 +1091,7 @@ qtl_status qtl_sesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlis
 
 qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tlist, int32_t nt, int32_t ntraj,
                         uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out, double* meas_out,
-                        qtl_stats* stats) {
+                        qtl_stats* stats, qtl_c128* traj_expect_out, double* traj_meas_out) {
     if (!sys || !psi0 || !tlist || nt < 1 || ntraj < 1 || !meas_out) return QTL_EINVAL;
     qtl_status st = check_opts(opts);
     if (st != QTL_OK) return st;
@@ -1159,9 +1159,16 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
         cudaStreamSynchronize(stream);
         return QTL_ECUDA;
     }
+    // per-trajectory values, [(k * nt + t) * ntraj + j]
+    std::vector<qtl_c128> tmh(traj_meas_out ? nm * ntraj : 0);
+    if (traj_expect_out && ne > 0)
+        QTL_CUDA(cudaMemcpyAsync(traj_expect_out, buf + o_te, ne * ntraj * 16, cudaMemcpyDeviceToHost, stream));
+    if (traj_meas_out)
+        QTL_CUDA(cudaMemcpyAsync(tmh.data(), buf + o_tm, nm * ntraj * 16, cudaMemcpyDeviceToHost, stream));
     cudaFreeAsync(buf, stream);
     QTL_CUDA(cudaStreamSynchronize(stream));
     for (size_t i = 0; i < nm; ++i) meas_out[i] = mh[i].re;
+    for (size_t i = 0; i < tmh.size(); ++i) traj_meas_out[i] = tmh[i].re;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->steps_acc = info.steps_acc;
@@ -1171,7 +1178,7 @@ qtl_status qtl_ssesolve(qtl_system* sys, const qtl_c128* psi0, const double* tli
 
 qtl_status qtl_smesolve(qtl_system* sys, int32_t n_sc, const qtl_c128* psi0, const double* tlist, int32_t nt,
                         int32_t ntraj, uint64_t seed, const qtl_opts* opts, qtl_c128* expect_out, double* meas_out,
-                        qtl_stats* stats) {
+                        qtl_stats* stats, qtl_c128* traj_expect_out, double* traj_meas_out) {
     if (!sys || !psi0 || !tlist || nt < 1 || ntraj < 1 || !meas_out) return QTL_EINVAL;
     qtl_status st = check_opts(opts);
     if (st != QTL_OK) return st;
@@ -1238,9 +1245,16 @@ qtl_status qtl_smesolve(qtl_system* sys, int32_t n_sc, const qtl_c128* psi0, con
         cudaStreamSynchronize(stream);
         return QTL_ECUDA;
     }
+    // per-trajectory values, [(k * nt + t) * ntraj + j]
+    std::vector<qtl_c128> tmh(traj_meas_out ? nm * ntraj : 0);
+    if (traj_expect_out && ne > 0)
+        QTL_CUDA(cudaMemcpyAsync(traj_expect_out, buf + o_te, ne * ntraj * 16, cudaMemcpyDeviceToHost, stream));
+    if (traj_meas_out)
+        QTL_CUDA(cudaMemcpyAsync(tmh.data(), buf + o_tm, nm * ntraj * 16, cudaMemcpyDeviceToHost, stream));
     cudaFreeAsync(buf, stream);
     QTL_CUDA(cudaStreamSynchronize(stream));
     for (size_t i = 0; i < nm; ++i) meas_out[i] = mh[i].re;
+    for (size_t i = 0; i < tmh.size(); ++i) traj_meas_out[i] = tmh[i].re;
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->steps_acc = info.steps_acc;

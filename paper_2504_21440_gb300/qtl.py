@@ -75,6 +75,13 @@ class SsStats(C.Structure):
                     cond_v=float(self.cond_v), gmres_residual=float(self.gmres_residual))
 
 
+class C128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+DSF_BUILD = C.CFUNCTYPE(C.c_int, C.POINTER(C128), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p))
+
+
 class DeviceInfo(C.Structure):
     _fields_ = [("status", C.c_int32), ("pad", C.c_int32), ("steps_acc", C.c_int64),
                 ("steps_rej", C.c_int64), ("rhs_evals", C.c_int64), ("jumps", C.c_int64)]
@@ -127,10 +134,10 @@ def load():
     lib.qtl_sesolve.argtypes = [P, P, P, C.c_int32, C.POINTER(Opts), P, C.POINTER(Stats)]
     lib.qtl_sesolve.restype = C.c_int
     lib.qtl_ssesolve.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(Opts), P, P,
-                                 C.POINTER(Stats)]
+                                 C.POINTER(Stats), P, P]
     lib.qtl_ssesolve.restype = C.c_int
     lib.qtl_smesolve.argtypes = [P, C.c_int32, P, P, C.c_int32, C.c_int32, C.c_uint64, C.POINTER(Opts), P, P,
-                                 C.POINTER(Stats)]
+                                 C.POINTER(Stats), P, P]
     lib.qtl_smesolve.restype = C.c_int
     lib.qtl_batch_create.argtypes = [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(Opts), P, P, C.c_int32,
                                      C.POINTER(P)]
@@ -156,6 +163,10 @@ def load():
     lib.qtl_steadystate_fourier.argtypes = [P, C.POINTER(Op), C.c_double, C.c_double, C.c_int32,
                                             C.POINTER(SsOpts), P, C.POINTER(SsStats)]
     lib.qtl_steadystate_fourier.restype = C.c_int
+    lib.qtl_dsf_mesolve.argtypes = [DSF_BUILD, P, C.c_int32, C.POINTER(Op), P, P, C.c_int32, P, C.c_int32,
+                                    C.c_double, C.POINTER(Opts), C.c_int32, P, P, C.POINTER(C.c_int32),
+                                    C.POINTER(Stats)]
+    lib.qtl_dsf_mesolve.restype = C.c_int
     lib.qtl_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(P)]
     lib.qtl_server_create.restype = C.c_int
     lib.qtl_server_submit.argtypes = [P, C.POINTER(Request), P, C.POINTER(C.c_uint64)]
@@ -289,33 +300,52 @@ def sesolve(sys, n_e, psi0, tlist, opts):
     return dict(expect=ex[:n_e], stats=st.as_dict())
 
 
-def ssesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts):
+def _traj_buffers(n_e, n_sc, nt, ntraj, keep):
+    if not keep:
+        return None, None
+    return (np.zeros((max(n_e, 1), nt, ntraj), dtype=np.complex128),
+            np.zeros((max(n_sc, 1), nt, ntraj), dtype=np.float64))
+
+
+def _with_traj(out, n_e, n_sc, te, tm):
+    if te is not None:
+        out["traj_expect"] = np.moveaxis(te[:n_e], 2, 0)        # [traj, e, t]
+        out["traj_measurement"] = np.moveaxis(tm[:n_sc], 2, 0)   # [traj, n, t]
+    return out
+
+
+def ssesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts, keep_trajectories=False):
     """qtl_ssesolve with host arrays.  Returns dict(expect[n_e, nt],
-    measurement[n_sc, nt], stats)."""
+    measurement[n_sc, nt], stats) and, with keep_trajectories, the
+    per-trajectory traj_expect[traj, e, t] and traj_measurement[traj, n, t]."""
     lib = load()
     p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
     tl = np.ascontiguousarray(tlist, dtype=np.float64)
     ex = np.zeros((max(n_e, 1), len(tl)), dtype=np.complex128)
     ms = np.zeros((max(n_sc, 1), len(tl)), dtype=np.float64)
+    te, tm = _traj_buffers(n_e, n_sc, len(tl), int(ntraj), keep_trajectories)
     st = Stats()
     _check(lib.qtl_ssesolve(sys, _ptr(p0), _ptr(tl), len(tl), int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
-                            C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st)), "qtl_ssesolve")
-    return dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict())
+                            C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st), _ptr(te), _ptr(tm)), "qtl_ssesolve")
+    return _with_traj(dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict()), n_e, n_sc, te, tm)
 
 
-def smesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts):
+def smesolve(sys, n_e, n_sc, psi0, tlist, ntraj, seed, opts, keep_trajectories=False):
     """qtl_smesolve with host arrays (the system's last n_sc collapse operators
-    are measured).  Returns dict(expect[n_e, nt], measurement[n_sc, nt], stats)."""
+    are measured).  Returns dict(expect[n_e, nt], measurement[n_sc, nt], stats)
+    and, with keep_trajectories, the per-trajectory values as ssesolve."""
     lib = load()
     p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
     tl = np.ascontiguousarray(tlist, dtype=np.float64)
     ex = np.zeros((max(n_e, 1), len(tl)), dtype=np.complex128)
     ms = np.zeros((max(n_sc, 1), len(tl)), dtype=np.float64)
+    te, tm = _traj_buffers(n_e, n_sc, len(tl), int(ntraj), keep_trajectories)
     st = Stats()
     _check(lib.qtl_smesolve(sys, int(n_sc), _ptr(p0), _ptr(tl), len(tl), int(ntraj),
-                            C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st)),
+                            C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts), _ptr(ex), _ptr(ms), C.byref(st),
+                            _ptr(te), _ptr(tm)),
            "qtl_smesolve")
-    return dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict())
+    return _with_traj(dict(expect=ex[:n_e], measurement=ms[:n_sc], stats=st.as_dict()), n_e, n_sc, te, tm)
 
 
 def system_free(sys):
@@ -588,6 +618,53 @@ def steadystate_fourier(sys, X, F, omega, nmax, opts):
     return dict(rho=rho, stats=st.as_dict())
 
 
+def dsf_mesolve(H_fn, c_fn, e_fn, op_list, alpha0, state0, tlist, threshold, **kw):
+    """qtl_dsf_mesolve.  H_fn(ops), c_fn(ops), e_fn(ops) build the Hamiltonian,
+    collapse operators and observables from ops = [a_k + alpha_k I]; the
+    library calls back whenever a coherence alpha_k changes.  op_list: the
+    mode operators a_k on the full space.  Returns dict(expect[k, t],
+    alpha[k, t], shifts, stats)."""
+    import scipy.sparse as sp
+    lib = load()
+    mods = [sp.csr_matrix(a, dtype=np.complex128) for a in op_list]
+    dim = mods[0].shape[0]
+    eye = sp.identity(dim, dtype=np.complex128, format="csr")
+    n_e = len(e_fn(mods))
+    errors = []
+
+    def build(alpha_p, n_modes, user, out):
+        try:
+            al = [complex(alpha_p[k].re, alpha_p[k].im) for k in range(n_modes)]
+            ops = [a + x * eye for a, x in zip(mods, al)]
+            out[0] = system_create(H_fn(ops), c_fn(ops), e_fn(ops)).value
+            return QTL_OK
+        except Exception as ex:   # reported after the call
+            errors.append(ex)
+            return QTL_EINVAL
+
+    cb = DSF_BUILD(build)
+    holders = [_OpHolder(a) for a in mods]
+    ops_arr = (Op * len(mods))(*[h.op for h in holders])
+    a0 = np.ascontiguousarray(np.asarray(alpha0, dtype=np.complex128))
+    s0 = np.ascontiguousarray(state0, dtype=np.complex128)
+    is_ket = 1 if s0.ndim == 1 else 0
+    if not is_ket:
+        s0 = np.ascontiguousarray(s0.reshape(-1, order="F"))
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt = len(tl)
+    ex = np.zeros((max(n_e, 1), nt), dtype=np.complex128)
+    al = np.zeros((len(mods), nt), dtype=np.complex128)
+    shifts = C.c_int32(0)
+    st = Stats()
+    status = lib.qtl_dsf_mesolve(cb, None, len(mods), ops_arr, _ptr(a0), _ptr(s0), is_ket, _ptr(tl), nt,
+                                 float(threshold), C.byref(make_opts(**kw)), n_e, _ptr(ex), _ptr(al),
+                                 C.byref(shifts), C.byref(st))
+    if errors:
+        raise errors[0]
+    _check(status, "qtl_dsf_mesolve")
+    return dict(expect=ex[:n_e], alpha=al, shifts=int(shifts.value), stats=st.as_dict())
+
+
 class System:
     """Owning wrapper: System(H, c_ops, e_ops) -> .mesolve(...) / .mcsolve(...)."""
 
@@ -607,13 +684,15 @@ class System:
     def mesolve(self, state0, tlist, save_states=False, **kw):
         return mesolve(self.handle, self.n_e, state0, tlist, make_opts(**kw), save_states)
 
-    def ssesolve(self, psi0, tlist, ntraj, seed, **kw):
+    def ssesolve(self, psi0, tlist, ntraj, seed, keep_trajectories=False, **kw):
         """The collapse operators given at construction are the stochastic operators."""
-        return ssesolve(self.handle, self.n_e, self.n_c, psi0, tlist, ntraj, seed, make_opts(**kw))
+        return ssesolve(self.handle, self.n_e, self.n_c, psi0, tlist, ntraj, seed, make_opts(**kw),
+                        keep_trajectories)
 
-    def smesolve(self, n_sc, psi0, tlist, ntraj, seed, **kw):
+    def smesolve(self, n_sc, psi0, tlist, ntraj, seed, keep_trajectories=False, **kw):
         """The last n_sc collapse operators given at construction are measured."""
-        return smesolve(self.handle, self.n_e, n_sc, psi0, tlist, ntraj, seed, make_opts(**kw))
+        return smesolve(self.handle, self.n_e, n_sc, psi0, tlist, ntraj, seed, make_opts(**kw),
+                        keep_trajectories)
 
     def sesolve(self, psi0, tlist, **kw):
         return sesolve(self.handle, self.n_e, psi0, tlist, make_opts(**kw))

@@ -48,10 +48,13 @@ def test_smesolve_matches_oracle(N, tl, dt):
     H, C, S, e_ops, psi0 = _jc(N)
     g = qtl.System(H, C + S, e_ops)
     try:
-        got = g.smesolve(1, psi0, tl, 2, 19, fixed_dt=dt)
+        got = g.smesolve(1, psi0, tl, 2, 19, fixed_dt=dt, keep_trajectories=True)
     finally:
         g.free()
-    ref = o_smesolve(H, C, S, e_ops, psi0, tl, dt, 2, 19)
+    ref = o_smesolve(H, C, S, e_ops, psi0, tl, dt, 2, 19, keep_trajectories=True)
+    # trajectory by trajectory (same Wiener increments), then the means
+    assert np.max(np.abs(got["traj_expect"] - ref["traj_expect"])) <= 1e-10
+    assert np.max(np.abs(got["traj_measurement"] - ref["traj_measurement"])) <= 1e-8
     assert np.max(np.abs(got["expect"] - ref["expect"])) <= 1e-10
     assert np.max(np.abs(got["measurement"] - ref["measurement"])) <= 1e-8
 

@@ -48,10 +48,13 @@ def test_ssesolve_matches_oracle(two):
     tl = np.linspace(0, 2, 5)
     g = qtl.System(H, sc, e_ops)
     try:
-        got = g.ssesolve(psi0, tl, 8, 21, fixed_dt=0.002)
+        got = g.ssesolve(psi0, tl, 8, 21, fixed_dt=0.002, keep_trajectories=True)
     finally:
         g.free()
-    ref = o_ssesolve(H, sc, e_ops, psi0, tl, 0.002, 8, 21)
+    ref = o_ssesolve(H, sc, e_ops, psi0, tl, 0.002, 8, 21, keep_trajectories=True)
+    # trajectory by trajectory (same Wiener increments), then the means
+    assert np.max(np.abs(got["traj_expect"] - ref["traj_expect"])) <= 1e-10
+    assert np.max(np.abs(got["traj_measurement"] - ref["traj_measurement"])) <= 1e-8
     assert np.max(np.abs(got["expect"] - ref["expect"])) <= 1e-10
     assert np.max(np.abs(got["measurement"] - ref["measurement"])) <= 1e-8
     assert got["stats"]["steps_acc"] == 8 * 1000
