@@ -408,6 +408,10 @@ typedef struct {
     int32_t restart;     /* Krylov vectors per cycle, 1..512 (default 60) */
     int32_t max_iter;    /* preconditioned matrix-vector products at most (default 20000) */
     void* cuda_stream;   /* cudaStream_t, NULL = the legacy default stream */
+    int32_t precision;   /* QTL_FP64 (default): FP64 preconditioner GEMMs; QTL_MIXED: on the
+                            tensor cores in split BF16 (qtl_zgemm_async), the Krylov
+                            vectors, products with L and residuals staying FP64 */
+    int32_t pad;
 } qtl_ss_opts;
 typedef struct {
     int32_t iterations;      /* preconditioned matrix-vector products */
@@ -420,6 +424,20 @@ void qtl_ss_opts_default(qtl_ss_opts* opts);
 qtl_status qtl_steadystate(qtl_system* sys, const qtl_ss_opts* opts, qtl_c128* rho_out, qtl_ss_stats* stats);
 qtl_status qtl_steadystate_fourier(qtl_system* sys, const qtl_op* X, double F, double omega, int32_t nmax,
                                    const qtl_ss_opts* opts, qtl_c128* rho_out, qtl_ss_stats* stats);
+
+/* Dense complex matrix product C = op(A) op(B) of n x n matrices (device
+ * pointers, column-major qtl_c128; op 0 = identity, 1 = conjugate
+ * transpose), the building block of the stationary-state preconditioner
+ * (no counterpart in the paper).  precision QTL_FP64: FP64 arithmetic.
+ * QTL_MIXED: on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation)
+ * with each entry split into two BF16 numbers and the three products
+ * hi*hi + hi*lo + lo*hi, about 2^-16 of sum_k |a_ik||b_kj| per entry.
+ * n <= 8192.  Enqueued on cuda_stream; scratch comes from the library's
+ * pool.  err_dev (device int, QTL_MIXED only, not cleared here) is set to 1
+ * if a wait inside the tensor-core kernel gave up (the result is then not
+ * valid).  QTL_ECUDA also when the driver offers no tensor-map encoder. */
+qtl_status qtl_zgemm_async(int32_t n, const qtl_c128* A, int32_t op_a, const qtl_c128* B, int32_t op_b,
+                           qtl_c128* C, int32_t precision, void* cuda_stream, int32_t* err_dev);
 
 /* ------------------------------------------- dynamical shifted Fock ---
  * dsf_mesolve (Sec. 3.6; Appendix B, Algorithm 1): the master equation in a
@@ -461,7 +479,10 @@ qtl_status qtl_dsf_mesolve(qtl_dsf_build_fn build, void* user, int32_t n_modes, 
  * arrival order while their estimated device memory fits the HBM budget;
  * each admitted request runs on its own CUDA stream, so requests that arrive
  * while others are on the GPU are admitted as memory frees up and their
- * kernels overlap.  Results are those of the corresponding qtl_mesolve /
+ * kernels overlap.  A request whose kernel occupies every SM (mesolve on the
+ * grid kernel, mcsolve above n = 1024) runs alone.  Submit builds the
+ * system's device structures for the request (on the caller's thread) before
+ * queueing it.  Results are those of the corresponding qtl_mesolve /
  * qtl_mcsolve call, bit for bit (each solve's arithmetic depends only on its
  * own inputs).  The caller's host buffers (state0, tlist, expect_out) must
  * stay valid until the request is done; the system must outlive it. */

@@ -310,6 +310,10 @@ cudaError_t launch_mc_wide(const McJob& job, int precision, const McWidePlan& pl
 
 // host helpers shared by the solve entry points (runtime.cpp)
 qtl_status ensure_liouvillian(System& s);
+// kind: QTL_REQ_MESOLVE | QTL_REQ_MCSOLVE; *fills_gpu (if non-null): the
+// solve's kernel occupies every SM (the cooperative grid mesolve, the
+// one-CTA-per-SM wide trajectory kernel)
+qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu = nullptr);
 void batch_plan(int L, int* C, int* rpt);
 int64_t cta_nnz_max(const System& s, int C);
 void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, const qtl_c128* state0_dev,
@@ -332,6 +336,10 @@ void csr_free(DevCsr& d);
 void ss_cache_free(System& s);   // steady.cu
 // C = op(A) op(B), n x n complex FP64, column-major, op: 0 identity, 1 conjugate transpose (steady.cu)
 cudaError_t launch_zgemm(int n, const double2* A, int ta, const double2* B, int tb, double2* C, cudaStream_t st);
+// the same product on the tensor cores, split BF16 (tc_gemm.cu)
+size_t tc_zgemm_scratch_bytes(int n);
+cudaError_t launch_tc_zgemm(int n, const double2* A, int opa, const double2* B, int opb, double2* C, void* scratch,
+                            int* err, cudaStream_t st);
 
 }  // namespace qtl
 

@@ -749,6 +749,34 @@ int64_t cta_nnz_max_of(const System& s, int C) {
 }
 
 // mesolve on the cooperative grid kernel (product form, no Liouvillian).
+// Builds, ahead of a solve, the device structures that solve will use
+// (Liouvillian, grid-kernel operators, sliced ELLPACK of A), so that a caller
+// such as the request server can do this host work outside its dispatcher.
+// The choice of engine repeats the one the solve makes.
+qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu) {
+    if (fills_gpu) *fills_gpu = 0;
+    if (kind == QTL_REQ_MCSOLVE) {
+        const bool wide = s.n > mc_traj_capacity() || o->engine == QTL_ENGINE_GRID;
+        if (fills_gpu) *fills_gpu = wide;
+        return wide ? ensure_sell(s) : QTL_OK;
+    }
+    if (s.n > 46340) return QTL_ETOOBIG;
+    qtl_status st;
+    if (!s.Htd.empty() && (st = ensure_td_liouvillian(s)) != QTL_OK) return st;
+    const int64_t L64 = (int64_t)s.n * s.n;
+    bool grid = o->engine == QTL_ENGINE_GRID || (o->engine == QTL_ENGINE_AUTO && L64 > me_cluster_capacity());
+    if (!grid) {
+        if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+        if (o->engine == QTL_ENGINE_AUTO) {
+            int C = 0, rpt = 0;
+            me_plan((int)L64, o->cluster_size, &C, &rpt);
+            grid = cta_nnz_max_of(s, C) > me_smem_nnz_budget(o->precision, rpt);
+        }
+    }
+    if (fills_gpu) *fills_gpu = grid;
+    return grid ? ensure_grid(s) : QTL_OK;
+}
+
 qtl_status mesolve_grid(System& s, const qtl_c128* state0_dev, int32_t is_ket, const double* tlist_dev,
                         int32_t nt, const qtl_opts* opts, qtl_c128* expect_dev, qtl_c128* states_dev,
                         qtl_device_info* info_dev) {

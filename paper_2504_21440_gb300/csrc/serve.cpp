@@ -1,7 +1,12 @@
 // Request server (qtl_server_*): a queue of mesolve / mcsolve requests
 // admitted in arrival order while their estimated device memory fits an HBM
 // budget, each admitted request running on its own CUDA stream so that work
-// from requests that arrived at different times overlaps on the GPU.
+// from requests that arrived at different times overlaps on the GPU.  A
+// request whose kernel occupies every SM (the cooperative grid mesolve, the
+// one-CTA-per-SM wide trajectory kernel) runs alone: overlap gains it
+// nothing, and other streams' kernels can hold back a cooperative launch.
+// The device structures of a request's system are built by submit, on the
+// caller's thread.
 //
 // One dispatcher thread owns the CUDA work: it admits requests (device
 // buffers from the stream-ordered pool, host->device copies, the _async
@@ -36,6 +41,7 @@ struct SrvReq {
     size_t bytes = 0;
     size_t ex_bytes = 0;
     int state = 0;  // 0 queued, 1 running, 2 done
+    int fills_gpu = 0;  // runs alone: its kernel occupies every SM
     int slot = -1;
     qtl_result res{};
 };
@@ -62,6 +68,7 @@ struct qtl_server {
     bool stop = false;
     uint64_t next_ticket = 1;
     int running = 0;
+    int exclusive = 0;   // a request whose kernel fills the GPU is running
 };
 
 namespace qtl {
@@ -227,6 +234,7 @@ static void srv_retire(qtl_server* S, int slot) {
     sl.req = nullptr;
     S->in_use -= q->bytes;
     S->running -= 1;
+    if (q->fills_gpu) S->exclusive = 0;
 }
 
 static void srv_loop(qtl_server* S) {
@@ -245,6 +253,11 @@ static void srv_loop(qtl_server* S) {
         while (!S->queue.empty()) {
             SrvReq* q = S->reqs[S->queue.front()];
             if (S->in_use + q->bytes > S->budget) break;
+            // a request whose kernel occupies every SM (a cooperative grid
+            // that must be resident at once, or one persistent CTA per SM)
+            // gains nothing from overlap and can be held back by it: it
+            // runs alone, and nothing is admitted beside it
+            if (S->exclusive || (q->fills_gpu && S->running > 0)) break;
             int slot = -1;
             for (size_t i = 0; i < S->slots.size(); ++i)
                 if (!S->slots[i].req) {
@@ -255,6 +268,7 @@ static void srv_loop(qtl_server* S) {
             S->queue.pop_front();
             S->in_use += q->bytes;
             S->running += 1;
+            if (q->fills_gpu) S->exclusive = 1;
             srv_admit(S, q, slot);
         }
         if (S->stop && S->running == 0) break;
@@ -312,7 +326,19 @@ qtl_status qtl_server_submit(qtl_server* S, const qtl_request* req, qtl_c128* ex
     if (st != QTL_OK) return st;
     for (int i = 1; i < req->nt; ++i)
         if (!(req->tlist[i] >= req->tlist[i - 1])) return QTL_EINVAL;
+    // the system's device structures are built here, on the caller's thread,
+    // not by the dispatcher while it holds the server
+    int fills = 0;
+    if ((st = prepare_solve(req->sys->s, req->kind, &req->opts, &fills)) != QTL_OK) return st;
+    if (wants_shadow(*req)) {
+        qtl_opts f = req->opts;
+        f.precision = QTL_FP64;
+        int f2 = 0;
+        if ((st = prepare_solve(req->sys->s, req->kind, &f, &f2)) != QTL_OK) return st;
+        fills |= f2;
+    }
     SrvReq* q = new SrvReq();
+    q->fills_gpu = fills;
     q->r = *req;
     q->expect_out = expect_out;
     q->bytes = request_bytes(*req);

@@ -188,6 +188,26 @@ cudaError_t launch_zgemm(int n, const double2* A, int ta, const double2* B, int 
     return cudaGetLastError();
 }
 
+// Y_z ./= lambda_i + conj(lambda_j) - i k_z w (the tensor-core path's division)
+__global__ void ss_divide_kernel(int n, int K, int kmid, double w, const double2* __restrict__ lam, double tiny,
+                                 double floor_den, double2* __restrict__ Y) {
+    const long long n2 = (long long)n * n;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= n2 * K) return;
+    const int z = (int)(e / n2);
+    const long long r = e - (long long)z * n2;
+    const int i = (int)(r % n), j = (int)(r / n);
+    const double2 li = lam[i], lj = lam[j];
+    double dr = li.x + lj.x, di = li.y - lj.y - (double)(z - kmid) * w;
+    if (hypot(dr, di) <= tiny) {
+        dr = floor_den;
+        di = 0.0;
+    }
+    const double q = 1.0 / (dr * dr + di * di);
+    const double2 c = Y[e];
+    Y[e] = make_double2((c.x * dr + c.y * di) * q, (c.y * dr - c.x * di) * q);
+}
+
 // partial[b][j] = sum over this block's rows of conj(V[r][j]) w[r], j < J
 __global__ void ss_mdot_kernel(long long N, int J, const double2* __restrict__ V, long long ldv,
                                const double2* __restrict__ w, double2* __restrict__ partial) {
@@ -264,6 +284,9 @@ struct SsSolver {
     double2 *Vk = nullptr, *Zk = nullptr, *x = nullptr, *b = nullptr, *wv = nullptr, *t1 = nullptr,
             *t2 = nullptr, *partial = nullptr, *hd = nullptr;
     int m = 60, nb = 128;
+    int mixed = 0;            // preconditioner GEMMs on the tensor cores (split BF16)
+    void* tcs = nullptr;      // their scratch
+    int* tc_err = nullptr;    // device flag of a tensor-core wait that gave up
     cudaError_t err = cudaSuccess;
 
     void chk(cudaError_t e) {
@@ -288,6 +311,22 @@ struct SsSolver {
     // out = S^-1 in, block by block
     void precond(const double2* in, double2* out) {
         const long long n2 = (long long)n * n;
+        if (mixed) {
+            for (int z = 0; z < K; ++z) {
+                const long long o = n2 * z;
+                chk(launch_tc_zgemm(n, pc->Vinv, 0, in + o, 0, t1 + o, tcs, tc_err, st));
+                chk(launch_tc_zgemm(n, t1 + o, 0, pc->Vinv, 1, t2 + o, tcs, tc_err, st));
+            }
+            count_launch();
+            ss_divide_kernel<<<grid(N), 256, 0, st>>>(n, K, kmid, w, pc->lam, pc->tiny, pc->floor_den, t2);
+            chk(cudaGetLastError());
+            for (int z = 0; z < K; ++z) {
+                const long long o = n2 * z;
+                chk(launch_tc_zgemm(n, pc->V, 0, t2 + o, 0, t1 + o, tcs, tc_err, st));
+                chk(launch_tc_zgemm(n, t1 + o, 0, pc->V, 1, out + o, tcs, tc_err, st));
+            }
+            return;
+        }
         gemm(pc->Vinv, 0, 0, in, n2, 0, t1, 0);     // V^-1 R
         gemm(t1, n2, 0, pc->Vinv, 0, 1, t2, 1);     // (V^-1 R V^-H) ./ D
         gemm(pc->V, 0, 0, t2, n2, 0, t1, 0);        // V Y
@@ -471,8 +510,10 @@ static qtl_status ss_run(System& s, int K, double w, const Csr* L1h, const qtl_s
     if (L1h && (st = csr_upload(*L1h, S.L1)) != QTL_OK) return st;
     const size_t vb = (size_t)S.N * sizeof(double2);
     char* buf = nullptr;
+    S.mixed = o->precision == QTL_MIXED;
+    const size_t tcb = S.mixed ? tc_zgemm_scratch_bytes(s.n) : 0;
     const size_t bytes = vb * ((size_t)2 * S.m + 6) + (size_t)S.nb * (S.m + 1) * sizeof(double2) +
-                         (size_t)(S.m + 1) * sizeof(double2) + 16 * 256;
+                         (size_t)(S.m + 1) * sizeof(double2) + tcb + 20 * 256;
     cudaError_t e = qtl_malloc_async((void**)&buf, bytes, S.st);
     if (e != cudaSuccess) {
         csr_free(S.L1);
@@ -494,6 +535,11 @@ static qtl_status ss_run(System& s, int K, double w, const Csr* L1h, const qtl_s
     S.t2 = carve(vb);
     S.partial = carve((size_t)S.nb * (S.m + 1) * sizeof(double2));
     S.hd = carve((size_t)(S.m + 1) * sizeof(double2));
+    if (S.mixed) {
+        S.tcs = carve(tcb);
+        S.tc_err = (int*)carve(sizeof(int));
+        S.chk(cudaMemsetAsync(S.tc_err, 0, sizeof(int), S.st));
+    }
     // b = e_0 of the k = 0 block
     S.chk(cudaMemsetAsync(S.b, 0, vb, S.st));
     const double2 one = make_double2(1.0, 0.0);
@@ -512,6 +558,9 @@ static qtl_status ss_run(System& s, int K, double w, const Csr* L1h, const qtl_s
         resid = xn > 0.0 ? rn / xn : rn;
         S.chk(cudaMemcpyAsync(rho_out, S.x, vb, cudaMemcpyDeviceToHost, S.st));
     }
+    int tc_fail = 0;
+    if (S.mixed && S.err == cudaSuccess)
+        S.chk(cudaMemcpyAsync(&tc_fail, S.tc_err, sizeof(int), cudaMemcpyDeviceToHost, S.st));
     S.chk(cudaFreeAsync(buf, S.st));
     S.chk(cudaStreamSynchronize(S.st));
     csr_free(S.L1);
@@ -519,6 +568,7 @@ static qtl_status ss_run(System& s, int K, double w, const Csr* L1h, const qtl_s
         set_cuda_error(S.err);
         return QTL_ECUDA;
     }
+    if (tc_fail) return QTL_ECUDA;
     if (stats) {
         stats->iterations = iters;
         stats->pad = 0;
@@ -531,6 +581,7 @@ static qtl_status ss_run(System& s, int K, double w, const Csr* L1h, const qtl_s
 
 static qtl_status check_ss_opts(const qtl_ss_opts* o) {
     if (!o || !(o->tol > 0.0) || o->restart < 1 || o->restart > 512 || o->max_iter < 1) return QTL_EINVAL;
+    if (o->precision != QTL_FP64 && o->precision != QTL_MIXED) return QTL_EINVAL;
     return QTL_OK;
 }
 
@@ -547,6 +598,7 @@ void qtl_ss_opts_default(qtl_ss_opts* o) {
     o->restart = 60;
     o->max_iter = 20000;
     o->cuda_stream = nullptr;
+    o->precision = QTL_FP64;
 }
 
 qtl_status qtl_steadystate(qtl_system* sys, const qtl_ss_opts* opts, qtl_c128* rho_out, qtl_ss_stats* stats) {

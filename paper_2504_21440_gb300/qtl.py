@@ -63,7 +63,7 @@ class Result(C.Structure):
 
 class SsOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int32), ("max_iter", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("precision", C.c_int32), ("pad", C.c_int32)]
 
 
 class SsStats(C.Structure):
@@ -163,6 +163,8 @@ def load():
     lib.qtl_steadystate_fourier.argtypes = [P, C.POINTER(Op), C.c_double, C.c_double, C.c_int32,
                                             C.POINTER(SsOpts), P, C.POINTER(SsStats)]
     lib.qtl_steadystate_fourier.restype = C.c_int
+    lib.qtl_zgemm_async.argtypes = [C.c_int32, P, C.c_int32, P, C.c_int32, P, C.c_int32, P, P]
+    lib.qtl_zgemm_async.restype = C.c_int
     lib.qtl_dsf_mesolve.argtypes = [DSF_BUILD, P, C.c_int32, C.POINTER(Op), P, P, C.c_int32, P, C.c_int32,
                                     C.c_double, C.POINTER(Opts), C.c_int32, P, P, C.POINTER(C.c_int32),
                                     C.POINTER(Stats)]
@@ -588,10 +590,11 @@ def mcsolve_noalloc(n, a_csr, c_csr, n_c, o_csr, n_e, psi0_dev, tlist_dev, ntraj
            "qtl_mcsolve_noalloc")
 
 
-def ss_opts(tol=1e-12, restart=60, max_iter=20000, stream=None):
+def ss_opts(tol=1e-12, restart=60, max_iter=20000, stream=None, precision="fp64"):
     o = SsOpts()
     load().qtl_ss_opts_default(C.byref(o))
     o.tol, o.restart, o.max_iter, o.cuda_stream = float(tol), int(restart), int(max_iter), stream
+    o.precision = PRECISIONS[precision]
     return o
 
 
@@ -616,6 +619,15 @@ def steadystate_fourier(sys, X, F, omega, nmax, opts):
            "qtl_steadystate_fourier")
     rho = {a - int(nmax): out[a * n * n:(a + 1) * n * n].reshape((n, n), order="F") for a in range(K)}
     return dict(rho=rho, stats=st.as_dict())
+
+
+def zgemm_async(A, B, C, op_a=0, op_b=0, precision="fp64", stream=None, err=None):
+    """qtl_zgemm_async on torch complex128 device tensors (n x n; column-major
+    storage, i.e. pass the transposes of row-major tensors): C = op(A) op(B).
+    err: a device int32 tensor (precision "mixed")."""
+    n = int(A.shape[0])
+    _check(load().qtl_zgemm_async(n, _ptr(A), int(op_a), _ptr(B), int(op_b), _ptr(C), PRECISIONS[precision],
+                                  stream, _ptr(err)), "qtl_zgemm_async")
 
 
 def dsf_mesolve(H_fn, c_fn, e_fn, op_list, alpha0, state0, tlist, threshold, **kw):
