@@ -24,6 +24,9 @@ import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
 
+from .integrate import Stats
+from .lindblad import effective_hamiltonian
+from .mcsolve import trajectory
 from .mesolve import mesolve
 
 
@@ -72,3 +75,58 @@ def dsf_mesolve(H_fn, c_fn, e_fn, op_list, alpha0, state0, tlist, threshold,
                 shifts += 1
         alphas[:, idx] = alpha
     return dict(expect=expect, alpha=alphas, shifts=shifts)
+
+
+def dsf_mcsolve(H_fn, c_fn, e_fn, op_list, alpha0, psi0, tlist, threshold, ntraj, seed,
+                method="tsit5", rtol=1e-8, atol=1e-10, keep_trajectories=False):
+    """Dynamical shifted Fock on quantum trajectories (Sec. 3.6 applies
+    Algorithm 1 of Appendix B to both solvers).  Each trajectory carries its
+    own frame alpha^(j): between checks it is the trajectory of mcsolve.py
+    under H_eff and the collapse operators built from a_k + alpha_k^(j) I
+    (its random stream and threshold carried over from check to check); at
+    each time of tlist the observables are recorded, then for each mode
+    d_k = <psi|a_k|psi>/<psi|psi> and, when |d_k| > threshold, the ket is
+    displaced, psi <- D_k(-d_k) psi, and alpha_k^(j) += d_k.  The readings of
+    dsf_mesolve (operator rebuild, displacement, check times) apply.
+    Returns dict(expect = mean over trajectories of the normalised
+    observables, traj_expect?, shifts, stats)."""
+    ops = [sp.csr_matrix(a, dtype=np.complex128) for a in op_list]
+    dim = ops[0].shape[0]
+    eye = sp.identity(dim, dtype=np.complex128, format="csr")
+    dense_a = [a.toarray() for a in ops]
+    tlist = np.asarray(tlist, dtype=np.float64)
+    nt = len(tlist)
+    n_e = len(e_fn(ops))
+    st = Stats()
+    per = []
+    shifts = 0
+    for j in range(ntraj):
+        alpha = np.array(alpha0, dtype=np.complex128)
+        psi = np.array(psi0, dtype=np.complex128)
+        state = None
+        ex = np.zeros((n_e, nt), dtype=np.complex128)
+        for idx in range(nt):
+            cur = [a + al * eye for a, al in zip(ops, alpha)]
+            if idx > 0:
+                c_cur = c_fn(cur)
+                out = {}
+                trajectory(effective_hamiltonian(H_fn(cur), c_cur), c_cur, [], psi,
+                           [tlist[idx - 1], tlist[idx]], seed, j, method, rtol, atol, stats=st,
+                           resume=state, state_out=out)
+                psi = out["psi"]
+                state = {"draws": out["draws"], "r": out["r"]}
+            nrm = np.vdot(psi, psi)
+            for k, O in enumerate(e_fn(cur)):
+                ex[k, idx] = np.vdot(psi, O @ psi) / nrm
+            for k, a in enumerate(dense_a):
+                d = np.vdot(psi, a @ psi) / nrm
+                if abs(d) > threshold:
+                    psi = sla.expm(-d * a.conj().T + np.conj(d) * a) @ psi   # D_k(-d)
+                    alpha[k] += d
+                    shifts += 1
+        per.append(ex)
+    per = np.array(per)
+    out = dict(expect=per.mean(axis=0), shifts=shifts, stats=st.as_dict())
+    if keep_trajectories:
+        out["traj_expect"] = per
+    return out

@@ -42,11 +42,16 @@ def _norm2(psi):
 
 def trajectory(Heff, c_ops, e_ops, psi0, tlist, seed, traj_id, method="tsit5",
                rtol=1e-8, atol=1e-10, fixed_dt=None, dt0=0.0, stats=None,
-               max_steps=10_000_000):
-    """One trajectory.  Returns (expect[k, t] complex, jump_times, jump_channels)."""
+               max_steps=10_000_000, resume=None, state_out=None):
+    """One trajectory.  Returns (expect[k, t] complex, jump_times, jump_channels).
+
+    resume: None, or dict(draws, r) to continue a trajectory whose random
+    stream has already given `draws` numbers and whose current threshold is r
+    (no new threshold is drawn at the start).  state_out: None, or a dict that
+    receives psi (at the last time of tlist), draws and r, for resuming."""
     tab = TABLEAUS[method]
     st = stats if stats is not None else Stats()
-    draws = [0]
+    draws = [0 if resume is None else int(resume["draws"])]
 
     def draw():
         u = uniform(seed, traj_id, draws[0])
@@ -62,7 +67,10 @@ def trajectory(Heff, c_ops, e_ops, psi0, tlist, seed, traj_id, method="tsit5",
 
     # without collapse operators there is no channel to jump to: the norm is
     # compared with a threshold of 0 (the first draw is still consumed)
-    r = [draw() if len(c_ops) > 0 else (draw(), 0.0)[1]]
+    if resume is not None:
+        r = [float(resume["r"])]
+    else:
+        r = [draw() if len(c_ops) > 0 else (draw(), 0.0)[1]]
     jump_times, jump_channels = [], []
     n_e = len(e_ops)
     expect = np.zeros((n_e, len(tlist)), dtype=np.complex128)
@@ -71,6 +79,8 @@ def trajectory(Heff, c_ops, e_ops, psi0, tlist, seed, traj_id, method="tsit5",
         nrm = np.vdot(psi, psi)
         for k, O in enumerate(e_ops):
             expect[k, idx] = np.vdot(psi, O @ psi) / nrm
+        if state_out is not None and idx == len(tlist) - 1:
+            state_out["psi"] = np.array(psi, dtype=np.complex128)
 
     def after_accept(t, y, k1, h, t_new, y_new, k_last):
         if _norm2(y_new) >= r[0]:
@@ -122,6 +132,9 @@ def trajectory(Heff, c_ops, e_ops, psi0, tlist, seed, traj_id, method="tsit5",
     integrate(f, np.asarray(psi0, dtype=np.complex128), tlist, tab, rtol, atol, on_save,
               dt0=dt0, fixed_dt=fixed_dt, max_steps=max_steps, after_accept=after_accept,
               stats=st)
+    if state_out is not None:
+        state_out["draws"] = draws[0]
+        state_out["r"] = r[0]
     return expect, jump_times, jump_channels
 
 

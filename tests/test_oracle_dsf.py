@@ -116,3 +116,99 @@ def test_two_displaced_modes_follow_the_linear_coherent_solution():
     assert np.min(np.max(np.abs(exact), axis=1)) > 1.5        # both modes leave the small cutoff
     assert np.max(np.abs(r["expect"] - exact)) <= 1e-6
     assert np.max(np.abs(r["alpha"] - exact)) <= 0.04
+
+
+# ------------------------------------------------------------ dsf_mcsolve
+from oracle.dsf import dsf_mcsolve  # noqa: E402
+from oracle.mcsolve import mcsolve  # noqa: E402
+
+
+def _cavity(N=8, D=0.5, F=7.0, kap=1.0):
+    a = destroy(N)
+    H = lambda o: D * (o[0].conj().T @ o[0]) + F * (o[0] + o[0].conj().T)
+    c = lambda o: [math.sqrt(kap) * o[0]]
+    e = lambda o: [o[0], o[0].conj().T @ o[0]]
+    return a, H, c, e
+
+
+def test_dsf_trajectories_of_a_driven_cavity_stay_coherent():
+    """A jump of sqrt(k) a leaves a coherent state unchanged, so every DSF
+    trajectory of the strongly driven cavity (about 98 photons, cutoff 8)
+    follows alpha(t) exactly, jumps and displacements included."""
+    N, D, F, kap = 8, 0.5, 7.0, 1.0
+    a, H, c, e = _cavity(N, D, F, kap)
+    tl = np.linspace(0.0, 3.0, 61)
+    r = dsf_mcsolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.05, ntraj=4, seed=3,
+                    rtol=1e-10, atol=1e-12, keep_trajectories=True)
+    ass = -1j * F / (kap / 2 + 1j * D)
+    al = ass * (1 - np.exp(-(kap / 2 + 1j * D) * tl))
+    assert r["stats"]["jumps"] > 10 and r["shifts"] > 100
+    for j in range(4):
+        assert np.max(np.abs(r["traj_expect"][j, 0] - al)) <= 1e-6
+        assert np.max(np.abs(r["traj_expect"][j, 1] - np.abs(al) ** 2)) <= 1e-5
+
+
+def test_dsf_mcsolve_with_an_unreached_threshold_is_mcsolve():
+    """No displacement: the DSF trajectories are mcsolve's trajectories with
+    the same random streams, integrated check to check."""
+    N = 6
+    a = destroy(N)
+    tl = np.linspace(0.0, 4.0, 9)
+    H = lambda o: 0.3 * (o[0].conj().T @ o[0]) + 0.4 * (o[0] + o[0].conj().T)
+    c = lambda o: [math.sqrt(0.5) * o[0]]
+    e = lambda o: [o[0], o[0].conj().T @ o[0]]
+    r = dsf_mcsolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 1e9, ntraj=6, seed=11,
+                    rtol=1e-10, atol=1e-12, keep_trajectories=True)
+    ref = mcsolve(H([a]), c([a]), e([a]), np.eye(N)[0], tl, ntraj=6, seed=11, rtol=1e-10, atol=1e-12,
+                  keep_trajectories=True)
+    assert r["shifts"] == 0
+    assert r["stats"]["jumps"] == ref["stats"]["jumps"] > 0
+    assert np.max(np.abs(r["traj_expect"] - ref["traj_expect"])) <= 1e-8
+
+
+def test_dsf_mcsolve_ensemble_matches_dsf_mesolve():
+    """A driven Kerr cavity (not coherent) with DSF: the trajectory mean is
+    within 4 sigma / sqrt(ntraj) of the DSF master equation, sigma the
+    spread of the real and imaginary parts separately.  The bound is 4, not 3,
+    because it is a maximum over 31 times and 3 components that are strongly
+    correlated; plain mcsolve on this cavity without shifts (cutoff 30) reaches
+    z = 3.3 at 80 trajectories with the same seed, and 400 trajectories stay
+    below z = 2.6, so the gap is statistical, not a bias."""
+    N, D, K, F, kap = 10, 0.5, 0.05, 3.0, 1.0
+    a = destroy(N)
+    tl = np.linspace(0.0, 3.0, 31)
+    H = lambda o: (D * (o[0].conj().T @ o[0]) + (K / 2) * (o[0].conj().T @ o[0].conj().T @ o[0] @ o[0])
+                   + F * (o[0] + o[0].conj().T))
+    c = lambda o: [math.sqrt(kap) * o[0]]
+    e = lambda o: [o[0].conj().T @ o[0], o[0]]
+    me = dsf_mesolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.1, rtol=1e-9, atol=1e-11)
+    ntraj = 80
+    r = dsf_mcsolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.1, ntraj=ntraj, seed=5,
+                    rtol=1e-9, atol=1e-11, keep_trajectories=True)
+    assert np.max(np.abs(me["expect"][0])) > 5.0        # beyond what the cutoff holds unshifted
+    for part in (np.real, np.imag):
+        sd = part(r["traj_expect"]).std(axis=0)
+        bound = 4 * np.maximum(sd, 1e-3) / math.sqrt(ntraj) + 1e-4
+        assert np.all(np.abs(part(r["expect"]) - part(me["expect"])) <= bound)
+
+
+def test_dsf_mcsolve_planted_sign_mistake_breaks_the_coherent_pin(monkeypatch):
+    """Displacing by D(+d) instead of D(-d), planted in a copy of the
+    oracle's displacement, loses the coherent state."""
+    import oracle.dsf as M
+    real = M.sla.expm
+
+    class _Flip:
+        @staticmethod
+        def expm(x):
+            return real(-x)
+
+    monkeypatch.setattr(M, "sla", _Flip)
+    N, D, F, kap = 8, 0.5, 7.0, 1.0
+    a, H, c, e = _cavity(N, D, F, kap)
+    tl = np.linspace(0.0, 1.0, 21)
+    r = dsf_mcsolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.05, ntraj=1, seed=3,
+                    rtol=1e-10, atol=1e-12)
+    ass = -1j * F / (kap / 2 + 1j * D)
+    al = ass * (1 - np.exp(-(kap / 2 + 1j * D) * tl))
+    assert np.max(np.abs(r["expect"][0] - al)) > 1e-2
