@@ -60,7 +60,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ising_c2",
-                    choices=["jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc", "optomech_td", "ssesolve_jc", "smesolve_jc"])
+                    choices=["ising_c2", "jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc",
+                             "optomech_td", "ssesolve_jc", "smesolve_jc", "steadystate", "dsf"])
     ap.add_argument("--rates", default="10,30,100,300")
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -872,6 +873,105 @@ def run_c2(args):
     g14.free()
 
 
+def run_steady(args):
+    """Stationary states (Sec. 3.2; Appendix A): a driven Kerr cavity with
+    N = 256 (65,536 unknowns: Delta = 0.5, K = 0.02, F = 2, kappa = 0.1) by
+    qtl_steadystate with the FP64 and with the tensor-core (split-BF16)
+    preconditioner, and the Fourier components (|k| <= 4) of the same cavity
+    at N = 40 under F cos(t)(a + a'), each timed over `steps` solves after
+    the warm-up (the first warm-up solve pays the host eigendecomposition,
+    timed separately).  The oracle's direct sparse solves are timed beside
+    them on the host, and the GPU results are compared with them."""
+    import torch
+    from paper_2504_21440_gb300 import qtl
+    from oracle.steadystate import steadystate as o_ss, steadystate_fourier as o_ssf
+    torch.cuda.set_device(0)
+    qtl.load()
+    out = {"metric": "stationary-state solves per second", "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "dtype": "f64 (preconditioner GEMMs f64 or split bf16)",
+           "data": "synthetic", "cases": {}}
+    s = W.kerr_cavity(256, 0.5, 0.02, 2.0, 0.1)
+    a = sp_destroy(40)
+    cases = [("kerr256", s.H, s.c_ops, None), ("kerr40_fourier", 0.5 * (a.conj().T @ a) + 0.01 * (a.conj().T @ a.conj().T @ a @ a),
+                                               [np.sqrt(0.2) * a], a + a.conj().T)]
+    for name, H, c, X in cases:
+        g = qtl.System(H, c, [])
+        t0 = time.perf_counter()
+        solve = (lambda **kw: g.steadystate(**kw)) if X is None else (lambda **kw: g.steadystate_fourier(X, 0.8, 1.0, 4, **kw))
+        solve()
+        t_setup = time.perf_counter() - t0
+        res = {"first_solve_s_with_setup": t_setup}
+        for prec in ("fp64", "mixed"):
+            for _ in range(max(0, args.warmup - 1)):
+                solve(precision=prec)
+            ts = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = solve(precision=prec)
+                ts.append(time.perf_counter() - t0)
+            res[prec] = {"s_per_solve": statistics.mean(ts), "solves_per_s": 1.0 / statistics.mean(ts),
+                         "iterations": r["stats"]["iterations"], "residual": r["stats"]["residual"]}
+            last = r
+        t0 = time.perf_counter()
+        ref = o_ss(H, c) if X is None else o_ssf(H, c, X, 0.8, 1.0, 4)
+        t_cpu = time.perf_counter() - t0
+        if X is None:
+            err = float(np.max(np.abs(last["rho"] - ref)))
+        else:
+            err = max(float(np.max(np.abs(last["rho"][k] - ref[k]))) for k in ref)
+        res["err_vs_oracle_direct_solve"] = err
+        res["cpu_baseline"] = {"s_per_solve": t_cpu, "kind": "oracle (SciPy direct sparse solve)", "cores": 1}
+        res["unknowns"] = int(H.shape[0] ** 2 * (1 if X is None else 9))
+        out["cases"][name] = res
+        g.free()
+    out["value"] = out["cases"]["kerr256"]["mixed"]["solves_per_s"]
+    print(json.dumps(out))
+
+
+def sp_destroy(N):
+    import scipy.sparse as sp
+    return sp.diags(np.sqrt(np.arange(1, N)), 1, format="csr", dtype=complex)
+
+
+def run_dsf(args):
+    """Dynamical shifted Fock mesolve (Sec. 3.6, Appendix B): the strongly
+    driven damped cavity (Delta = 0.5, F = 7, kappa = 1, about 98 photons)
+    followed at a Fock cutoff of 8, t in [0, 6] with 301 checks, threshold
+    0.05, rtol 1e-10 atol 1e-12, timed over `steps` runs; the oracle on one
+    core beside it, and the largest difference from it."""
+    from paper_2504_21440_gb300 import qtl
+    from oracle.dsf import dsf_mesolve as o_dsf
+    qtl.load()
+    N, D, F, kap = 8, 0.5, 7.0, 1.0
+    a = sp_destroy(N)
+    tl = np.linspace(0.0, 6.0, 301)
+    H = lambda o: D * (o[0].conj().T @ o[0]) + F * (o[0] + o[0].conj().T)
+    c = lambda o: [np.sqrt(kap) * o[0]]
+    e = lambda o: [o[0], o[0].conj().T @ o[0]]
+    tol = dict(rtol=1e-10, atol=1e-12)
+    for _ in range(args.warmup):
+        qtl.dsf_mesolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.05, **tol)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = qtl.dsf_mesolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.05, **tol)
+        ts.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    ref = o_dsf(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.05, **tol)
+    t_cpu = time.perf_counter() - t0
+    m = statistics.mean(ts)
+    print(json.dumps({"metric": "dsf_mesolve solves per second", "value": 1.0 / m, "unit": "solves/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+                      "data": "synthetic", "s_per_solve": m, "shifts": r["shifts"], "rhs_evals": r["stats"]["rhs_evals"],
+                      "config": {"workload": "dsf driven cavity: N=8, Delta=0.5, F=7, kappa=1, t in [0,6], 301 checks, "
+                                             "threshold 0.05, rtol 1e-10 atol 1e-12"},
+                      "err_vs_oracle": float(max(np.max(np.abs(r["expect"] - ref["expect"])),
+                                                 np.max(np.abs(r["alpha"] - ref["alpha"])))),
+                      "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                       "sample": "one full solve"}}))
+
+
 def run_ising14_mc(args):
     """mcsolve on the dissipative transverse-field Ising chain of 14 spins
     (n = 16,384; H_eff with 245,760 entries), h from seed 3, gamma = 0.1, all
@@ -1290,7 +1390,7 @@ def main():
         return
     if args.impl == "reference" and args.workload != "jc_40x2":
         # the other workloads time the oracle in their own cpu_baseline entry
-        sys.exit("bench.py: --impl reference times the jc_40x2 job; the line of --workload %s "
+        sys.exit("bench.py: --impl reference times the ising_c2 and jc_40x2 jobs; the line of --workload %s "
                  "carries its own oracle timing (cpu_baseline)" % args.workload)
     if args.workload not in SHARDED and int(os.environ.get("WORLD_SIZE", "1")) > 1:
         sys.exit("bench.py: --workload %s runs on one GPU (no torchrun)" % args.workload)
@@ -1302,6 +1402,12 @@ def main():
         return
     if args.workload == "optomech_td" and args.impl != "reference":
         run_optomech(args)
+        return
+    if args.workload == "steadystate" and args.impl != "reference":
+        run_steady(args)
+        return
+    if args.workload == "dsf" and args.impl != "reference":
+        run_dsf(args)
         return
     if args.workload == "serving" and args.impl != "reference":
         run_serving(args)

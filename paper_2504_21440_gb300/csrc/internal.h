@@ -309,7 +309,10 @@ cudaError_t launch_mc_wide(const McJob& job, int precision, const McWidePlan& pl
                            const SellConst* cdesc, cudaStream_t st);
 
 // host helpers shared by the solve entry points (runtime.cpp)
-qtl_status ensure_liouvillian(System& s);
+// CSR Liouvillian (FP64, column stacking) on the device, built once per
+// system; ETOOBIG when n^2 exceeds max_rows (default: the cluster kernel's
+// capacity).
+qtl_status ensure_liouvillian(System& s, int64_t max_rows = -1);
 // kind: QTL_REQ_MESOLVE | QTL_REQ_MCSOLVE; *fills_gpu (if non-null): the
 // solve's kernel occupies every SM (the cooperative grid mesolve, the
 // one-CTA-per-SM wide trajectory kernel)

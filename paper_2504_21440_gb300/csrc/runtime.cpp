@@ -673,10 +673,13 @@ static qtl_status ensure_td_liouvillian(System& s) {
     return upload_csr(stacked, s.dTL);
 }
 
-qtl_status ensure_liouvillian(System& s) {
+qtl_status ensure_liouvillian(System& s, int64_t max_rows) {
+    // The size bound is checked before the cache: a Liouvillian built for a
+    // larger caller (the stationary-state solver) is not handed to the
+    // cluster kernels, whose bound is the default.
+    if ((int64_t)s.n * s.n > (max_rows < 0 ? (int64_t)me_cluster_capacity() : max_rows)) return QTL_ETOOBIG;
     std::lock_guard<std::mutex> lk(g_build_mu);
     if (s.dL.rp) return QTL_OK;
-    if ((int64_t)s.n * s.n > me_cluster_capacity()) return QTL_ETOOBIG;
     Csr L;
     build_liouvillian(s, L);
     if (L.nnz() >= (int64_t)INT32_MAX) return QTL_ETOOBIG;

@@ -495,7 +495,7 @@ static qtl_status ensure_ss_cache(System& s) {
 static qtl_status ss_run(System& s, int K, double w, const Csr* L1h, const qtl_ss_opts* o,
                          qtl_c128* rho_out, qtl_ss_stats* stats) {
     qtl_status st;
-    if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+    if ((st = ensure_liouvillian(s, (int64_t)QTL_SS_MAX_N * QTL_SS_MAX_N)) != QTL_OK) return st;
     if ((st = ensure_ss_cache(s)) != QTL_OK) return st;
     SsSolver S;
     S.n = s.n;

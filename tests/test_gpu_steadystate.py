@@ -130,3 +130,29 @@ def test_steadystate_edge_cases():
         assert e.value.status == qtl.QTL_ETOOBIG
     finally:
         big.free()
+
+
+def test_steadystate_beyond_the_cluster_kernel_capacity():
+    """A Kerr cavity at N = 132 (17,424 unknowns, above the 16,384 rows the
+    cluster mesolve kernel holds) in FP64 and with the split-BF16
+    preconditioner; the system's mesolve afterwards still refuses the cluster
+    engine and runs on the grid engine."""
+    qtl = require_gpu()
+    H, c = _kerr(N=132, D=0.5, K=0.02, F=1.5, kap=0.2)
+    ref = o_ss(H, c)
+    g = qtl.System(H, c, [c[0].conj().T @ c[0]])
+    try:
+        for prec in ("fp64", "mixed"):
+            got = g.steadystate(precision=prec)
+            assert maxabs(got["rho"], ref) <= 1e-10, prec
+            assert got["stats"]["residual"] <= 1e-11, prec
+        rho0 = np.zeros((132, 132), complex)
+        rho0[0, 0] = 1.0
+        tl = np.linspace(0.0, 0.5, 3)
+        with pytest.raises(qtl.QtlError) as e:
+            g.mesolve(rho0, tl, engine="cluster")
+        assert e.value.status == qtl.QTL_ETOOBIG
+        out = g.mesolve(rho0, tl, engine="grid")
+        assert np.all(np.isfinite(out["expect"]))
+    finally:
+        g.free()

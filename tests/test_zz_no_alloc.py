@@ -98,3 +98,48 @@ def test_noalloc_reports_a_malformed_operator_in_its_status():
         qtl.mcsolve_noalloc(s.n, a, c, len(s.c_ops), o, len(s.e_ops), psi, tl, 4, 1, opts, ex, info)
         torch.cuda.synchronize(dev)
         assert int(info.cpu().numpy()[0]) & 0xffffffff == qtl.QTL_EINVAL
+
+
+def test_noalloc_call_captured_in_a_cuda_graph():
+    """One warm call, then a call captured into a CUDA graph on a side stream
+    (global capture mode) and replayed twice: each replay gives the
+    allocating entry point's ensemble (the captured host steps set function
+    attributes and query occupancy, which capture allows, and allocate
+    nothing)."""
+    qtl = require_gpu()
+    import torch
+    dev = torch.device("cuda:0")
+    s = W.jaynes_cummings(N=10, nt=41, t_end=60.0, kappa=0.1, gamma=0.05)
+    ntraj, seed = 64, 11
+    tol = dict(precision="fp64", rtol=1e-8, atol=1e-10)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    ref = g.mcsolve(s.psi0, s.tlist, ntraj, seed, **tol)
+    g.free()
+    a = _dev_csr((-1j * effective_hamiltonian(s.H, s.c_ops)).tocsr(), dev)
+    c = _dev_csr(sp.vstack(s.c_ops), dev)
+    o = _dev_csr(sp.vstack(s.e_ops), dev)
+    psi = torch.from_numpy(s.psi0).to(dev)
+    tl = torch.from_numpy(s.tlist).to(dev)
+    ex = torch.zeros((len(s.e_ops), len(s.tlist)), dtype=torch.complex128, device=dev)
+    info = torch.zeros(5, dtype=torch.int64, device=dev)
+
+    def call(stream):
+        qtl.mcsolve_noalloc(s.n, a, c, len(s.c_ops), o, len(s.e_ops), psi, tl, ntraj, seed,
+                            qtl.make_opts(stream=stream.cuda_stream, **tol), ex, info)
+
+    call(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        call(side)
+    for _ in range(2):
+        ex.fill_(float("nan"))
+        info.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize(dev)
+        inf = info.cpu().numpy()
+        assert int(inf[0]) & 0xffffffff == 0
+        assert int(inf[4]) > 0
+        assert maxabs(ex.cpu().numpy(), ref["expect"]) <= 1e-8
