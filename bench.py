@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ising_c2",
                     choices=["ising_c2", "jc_40x2", "kerr_sweep_1024", "serving", "ising10", "ising14_mc",
-                             "optomech_td", "ssesolve_jc", "smesolve_jc", "steadystate", "dsf"])
+                             "optomech_td", "ssesolve_jc", "smesolve_jc", "steadystate", "dsf", "dsf_mc"])
     ap.add_argument("--rates", default="10,30,100,300")
     ap.add_argument("--requests", type=int, default=120)
     return ap.parse_args()
@@ -972,6 +972,50 @@ def run_dsf(args):
                                        "sample": "one full solve"}}))
 
 
+def run_dsf_mc(args):
+    """Dynamical shifted Fock on quantum trajectories (Sec. 3.6, Appendix B
+    applied per trajectory): a driven Kerr cavity (Delta = 0.5, K = 0.05,
+    F = 3, kappa = 1, <n> up to about 12) at a Fock cutoff of 10, t in [0, 6]
+    with 61 checks, threshold 0.1, 256 trajectories, FP64, rtol 1e-9 atol
+    1e-11, timed over `steps` runs.  The oracle runs the first 4 trajectories
+    (the same Philox streams) on one core: its rate beside the GPU's, and the
+    largest difference between the two trajectory by trajectory."""
+    from paper_2504_21440_gb300 import qtl
+    from oracle.dsf import dsf_mcsolve as o_dsf_mc
+    qtl.load()
+    N, D, K, F, kap = 10, 0.5, 0.05, 3.0, 1.0
+    a = sp_destroy(N)
+    tl = np.linspace(0.0, 6.0, 61)
+    H = lambda o: (D * (o[0].conj().T @ o[0]) + (K / 2) * (o[0].conj().T @ o[0].conj().T @ o[0] @ o[0])
+                   + F * (o[0] + o[0].conj().T))
+    c = lambda o: [np.sqrt(kap) * o[0]]
+    e = lambda o: [o[0].conj().T @ o[0], o[0]]
+    tol = dict(rtol=1e-9, atol=1e-11)
+    ntraj, nsample = 256, 4
+    run = lambda: qtl.dsf_mcsolve(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.1, ntraj, 5, keep_trajectories=True, **tol)
+    for _ in range(args.warmup):
+        run()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = run()
+        ts.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    ref = o_dsf_mc(H, c, e, [a], [0.0], np.eye(N)[0], tl, 0.1, ntraj=nsample, seed=5, keep_trajectories=True, **tol)
+    t_cpu = time.perf_counter() - t0
+    m = statistics.mean(ts)
+    print(json.dumps({"metric": "dsf_mcsolve trajectories per second", "value": ntraj / m, "unit": "traj/s",
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                      "dtype": "f64", "data": "synthetic", "s_per_solve": m, "shifts": r["shifts"],
+                      "jumps": r["stats"]["jumps"], "rhs_evals": r["stats"]["rhs_evals"],
+                      "config": {"workload": "dsf_mcsolve driven Kerr cavity: N=10, Delta=0.5, K=0.05, F=3, kappa=1, "
+                                             "t in [0,6], 61 checks, threshold 0.1, 256 trajectories (seed 5), "
+                                             "rtol 1e-9 atol 1e-11"},
+                      "err_vs_oracle_first4traj": float(np.max(np.abs(r["traj_expect"][:nsample] - ref["traj_expect"]))),
+                      "cpu_baseline": {"value": nsample / t_cpu, "unit": "traj/s", "cores": 1, "kind": "oracle",
+                                       "sample": f"the first {nsample} of the {ntraj} trajectories"}}))
+
+
 def run_ising14_mc(args):
     """mcsolve on the dissipative transverse-field Ising chain of 14 spins
     (n = 16,384; H_eff with 245,760 entries), h from seed 3, gamma = 0.1, all
@@ -1405,6 +1449,9 @@ def main():
         return
     if args.workload == "steadystate" and args.impl != "reference":
         run_steady(args)
+        return
+    if args.workload == "dsf_mc" and args.impl != "reference":
+        run_dsf_mc(args)
         return
     if args.workload == "dsf" and args.impl != "reference":
         run_dsf(args)

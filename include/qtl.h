@@ -473,6 +473,36 @@ qtl_status qtl_dsf_mesolve(qtl_dsf_build_fn build, void* user, int32_t n_modes, 
                            int32_t nt, double threshold, const qtl_opts* opts, int32_t n_e, qtl_c128* expect_out,
                            qtl_c128* alpha_out, int32_t* shifts, qtl_stats* stats);
 
+/* dsf_mcsolve (Sec. 3.6 applies Algorithm 1 of Appendix B to quantum
+ * trajectories as well): the trajectories of qtl_mcsolve, each in its own
+ * displaced frame alpha^(j).  Between the times of tlist every trajectory is
+ * integrated (one launch of the trajectory kernel for all of them) with the
+ * operators built for its own frame, its Philox stream (seed, trajectory
+ * index j) and jump threshold carrying over from interval to interval, and
+ * each interval starting with the starting-step heuristic.  At every time of
+ * tlist the normalised observables are recorded, then for each mode
+ * d_k = <psi|a_k|psi>/<psi|psi> of each trajectory and, when |d_k| >
+ * threshold, psi <- exp(-d_k a_k^H + conj(d_k) a_k) psi (in the truncated
+ * space, on the device), alpha_k^(j) += d_k, and the trajectory's system is
+ * rebuilt by build (as for qtl_dsf_mesolve; until its first displacement a
+ * trajectory uses the system built for alpha0).
+ *   modes[n_modes]   a_k on the full space (n x n, n <= 1024), 1 <= n_modes <= 16
+ *   alpha0, psi0     initial coherences and ket (n entries, in the frame of alpha0)
+ *   ntraj, seed      trajectories 0..ntraj-1 of the Philox streams of seed
+ *   opts             as for qtl_mcsolve; the grid engine is refused
+ *   n_e              observables of the systems build returns (checked)
+ *   expect_out[n_e*nt]             trajectory means (before each time's shift)
+ *   traj_expect_out[ntraj*n_e*nt]  (or NULL) per trajectory, [j][e][t]
+ *   shifts (or NULL): displacements applied, over all trajectories and modes
+ * Host pointers; returns when done.  Errors: QTL_EINVAL (arguments, a built
+ * system of another dimension, observable or collapse-operator count, or
+ * with time-dependent terms), QTL_ETOOBIG (n > 1024), build's own status,
+ * the solve's status (QTL_ESTEP), QTL_ENOMEM, QTL_ECUDA. */
+qtl_status qtl_dsf_mcsolve(qtl_dsf_build_fn build, void* user, int32_t n_modes, const qtl_op* modes,
+                           const qtl_c128* alpha0, const qtl_c128* psi0, const double* tlist, int32_t nt,
+                           double threshold, int32_t ntraj, uint64_t seed, const qtl_opts* opts, int32_t n_e,
+                           qtl_c128* expect_out, qtl_c128* traj_expect_out, int64_t* shifts, qtl_stats* stats);
+
 /* ------------------------------------------------------------- serving ---
  * A request server (no counterpart in the paper; it serves the mesolve and
  * mcsolve calls above).  Requests are queued on submit and admitted in

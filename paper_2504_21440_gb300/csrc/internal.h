@@ -213,6 +213,22 @@ struct MgJob {
     int method;
 };
 
+// Operators of one trajectory (DSF on trajectories: each trajectory carries
+// its own frame, so its own A = -i H_eff, collapse operators and
+// observables); device pointers into that trajectory's system.
+struct McTrajOps {
+    const int4* aseg;
+    const int32_t* aci;
+    const double2* av64;
+    const float2* av32;
+    const int32_t* crp;
+    const int32_t* cci;
+    const double2* cv;
+    const int32_t* orp;
+    const int32_t* oci;
+    const double2* ov;
+};
+
 struct McJob {
     int n;
     int a_nnz;            // entries of A
@@ -271,6 +287,12 @@ struct McJob {
     int xsmem;             // stage inputs in shared memory (1) or in wscr (0)
     int xbufs;             // stage-input buffers in shared memory (1 or 2)
     int* wnext;            // trajectory counter (zero at launch), or null: static assignment
+    // trajectory kernel, resumable trajectories (null / 0: off)
+    const McTrajOps* tops;  // [ntraj]: trajectory jt's own operators instead of the job's
+    long long psi0_stride;  // elements between the trajectories' initial kets (0: one shared ket)
+    double2* psi_out;       // [ntraj][n]: the unnormalised ket at the last time of tlist
+    unsigned* rng_draw;     // [ntraj] in/out: Philox draw counter; 0 = start the stream
+    double* rng_r;          // [ntraj] in/out: the current jump threshold (when rng_draw > 0)
 };
 
 // Launch plan of the wide trajectory kernel: grid, shared memory and the

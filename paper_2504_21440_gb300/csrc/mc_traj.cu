@@ -58,12 +58,18 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
         }
         __syncthreads();
     }
+    // operators: the job's, or (J.tops) the current trajectory's own
+    const int4* Aseg = J.aseg;
+    const int32_t* Aci = J.aci;
+    const TV* Av = av;
+    const int32_t *Crp = J.crp, *Cci = J.cci, *Orp = J.orp, *Oci = J.oci;
+    const double2 *Cv = J.cv, *Ov = J.ov;
     // A x, plus sum_k f_k(t) (-i H_k) x with the coefficients of slot `slot`
     // (1..6: the stages of the current step, 7: one other time)
     const TV* tv = MIXED ? (const TV*)J.tv32 : (const TV*)J.tv64;
     auto rhs_row = [&](int r, const T2* x, int slot) -> T2 {
         T2 v = cached ? mc_spmv_row_s<T2, TV>(r, s_seg, s_ci, s_v, x)
-                      : mc_spmv_row<T2, TV>(r, J.aseg, J.aci, av, x);
+                      : mc_spmv_row<T2, TV>(r, Aseg, Aci, Av, x);
         for (int k = 0; k < J.n_td; ++k) {
             const T2 w = mc_spmv_row<T2, TV>(k * n + r, J.tseg, J.tci, tv, x);
             T2 f;
@@ -90,6 +96,18 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
 
     for (int jt = blockIdx.x; jt < J.ntraj; jt += gridDim.x) {
         const unsigned long long traj = (unsigned long long)(J.traj_offset + jt);
+        if (J.tops) {
+            const McTrajOps o = J.tops[jt];
+            Aseg = o.aseg;
+            Aci = o.aci;
+            Av = MIXED ? (const TV*)o.av32 : (const TV*)o.av64;
+            Crp = o.crp;
+            Cci = o.cci;
+            Cv = o.cv;
+            Orp = o.orp;
+            Oci = o.oci;
+            Ov = o.ov;
+        }
         double2 y[RPT], ynew[RPT];
         float2 yf[RPT], yfn[RPT];
         T2 k[7][RPT];
@@ -111,7 +129,7 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
         for (int m = 0; m < RPT; ++m) {
             row[m] = tid + m * T_;
             own[m] = row[m] < n;
-            y[m] = own[m] ? J.psi0[row[m]] : make_double2(0.0, 0.0);
+            y[m] = own[m] ? J.psi0[(size_t)jt * J.psi0_stride + row[m]] : make_double2(0.0, 0.0);
             ynew[m] = y[m];
             yfn[m] = make_float2(0.f, 0.f);
             if (own[m]) {
@@ -164,9 +182,9 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                     if (!own[m]) continue;
                     const int i = e * n + row[m];
                     double ox = 0.0, oy = 0.0;
-                    for (int p = __ldg(J.orp + i); p < __ldg(J.orp + i + 1); ++p) {
-                        const double2 o = J.ov[p];
-                        const double2 v = yd[__ldg(J.oci + p)];
+                    for (int p = __ldg(Orp + i); p < __ldg(Orp + i + 1); ++p) {
+                        const double2 o = Ov[p];
+                        const double2 v = yd[__ldg(Oci + p)];
                         ox += o.x * v.x - o.y * v.y;
                         oy += o.x * v.y + o.y * v.x;
                     }
@@ -195,8 +213,14 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
         CtlF ctl;
         ctl.init();
         if (tid == 0) {
-            r = philox_uniform(J.seed, traj, draw++);
-            if (J.n_c == 0) r = 0.0;   // no channel to jump to: never below the threshold
+            if (J.rng_draw && J.rng_draw[jt] > 0) {
+                // resumed trajectory: its stream and threshold carry over
+                draw = J.rng_draw[jt];
+                r = J.rng_r[jt];
+            } else {
+                r = philox_uniform(J.seed, traj, draw++);
+                if (J.n_c == 0) r = 0.0;   // no channel to jump to: never below the threshold
+            }
             rhs_evals += 1;
         }
         // ---- starting step ----
@@ -571,9 +595,9 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                     if (!own[m]) continue;
                     const int i = c * n + row[m];
                     double vx = 0.0, vy = 0.0;
-                    for (int p = __ldg(J.crp + i); p < __ldg(J.crp + i + 1); ++p) {
-                        const double2 cv = J.cv[p];
-                        const double2 v = yd[__ldg(J.cci + p)];
+                    for (int p = __ldg(Crp + i); p < __ldg(Crp + i + 1); ++p) {
+                        const double2 cv = Cv[p];
+                        const double2 v = yd[__ldg(Cci + p)];
                         vx += cv.x * v.x - cv.y * v.y;
                         vy += cv.x * v.y + cv.y * v.x;
                     }
@@ -613,9 +637,9 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                     if (!own[m]) continue;
                     const int i = ch * n + row[m];
                     double vx = 0.0, vy = 0.0;
-                    for (int p = __ldg(J.crp + i); p < __ldg(J.crp + i + 1); ++p) {
-                        const double2 cv = J.cv[p];
-                        const double2 v = yd[__ldg(J.cci + p)];
+                    for (int p = __ldg(Crp + i); p < __ldg(Crp + i + 1); ++p) {
+                        const double2 cv = Cv[p];
+                        const double2 v = yd[__ldg(Cci + p)];
                         vx += cv.x * v.x - cv.y * v.y;
                         vy += cv.x * v.y + cv.y * v.x;
                     }
@@ -634,6 +658,16 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
             norm2_ynew(&n2);  // ynew == y here: |psi|^2 after the jump
             if (tid == 0) norm2 = n2;
             __syncthreads();
+        }
+        // resumable trajectories: the ket at the last time and the stream
+        if (J.psi_out) {
+#pragma unroll
+            for (int m = 0; m < RPT; ++m)
+                if (own[m]) J.psi_out[(size_t)jt * n + row[m]] = y[m];
+        }
+        if (J.rng_draw && tid == 0) {
+            J.rng_draw[jt] = draw;
+            J.rng_r[jt] = r;
         }
         __syncthreads();
     }
@@ -738,7 +772,8 @@ cudaError_t launch_mc_traj(const McJob& J0, int precision, cudaStream_t st) {
     const size_t tv = precision == QTL_MIXED ? sizeof(float2) : sizeof(double2);
     const size_t base = (size_t)J.n * (sizeof(double2) + 2 * tv) + 64 +
                         (size_t)(sh.T / 32 + 1) * mc_red_stride(J.n_e, J.n_c) * sizeof(double);
-    J.a_smem = base + 16 + (size_t)J.n * sizeof(int4) + (size_t)J.a_nnz * (tv + 4) <= 200 * 1024;
+    // (not with per-trajectory operators: the copy is made once per CTA)
+    J.a_smem = !J.tops && base + 16 + (size_t)J.n * sizeof(int4) + (size_t)J.a_nnz * (tv + 4) <= 200 * 1024;
     return precision == QTL_MIXED ? mc_dispatch<true>(J, sh, st) : mc_dispatch<false>(J, sh, st);
 }
 

@@ -169,6 +169,10 @@ def load():
                                     C.c_double, C.POINTER(Opts), C.c_int32, P, P, C.POINTER(C.c_int32),
                                     C.POINTER(Stats)]
     lib.qtl_dsf_mesolve.restype = C.c_int
+    lib.qtl_dsf_mcsolve.argtypes = [DSF_BUILD, P, C.c_int32, C.POINTER(Op), P, P, P, C.c_int32, C.c_double,
+                                    C.c_int32, C.c_uint64, C.POINTER(Opts), C.c_int32, P, P,
+                                    C.POINTER(C.c_int64), C.POINTER(Stats)]
+    lib.qtl_dsf_mcsolve.restype = C.c_int
     lib.qtl_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(P)]
     lib.qtl_server_create.restype = C.c_int
     lib.qtl_server_submit.argtypes = [P, C.POINTER(Request), P, C.POINTER(C.c_uint64)]
@@ -675,6 +679,54 @@ def dsf_mesolve(H_fn, c_fn, e_fn, op_list, alpha0, state0, tlist, threshold, **k
         raise errors[0]
     _check(status, "qtl_dsf_mesolve")
     return dict(expect=ex[:n_e], alpha=al, shifts=int(shifts.value), stats=st.as_dict())
+
+
+def dsf_mcsolve(H_fn, c_fn, e_fn, op_list, alpha0, psi0, tlist, threshold, ntraj, seed,
+                keep_trajectories=False, **kw):
+    """qtl_dsf_mcsolve: DSF on quantum trajectories, each in its own frame.
+    H_fn, c_fn, e_fn and op_list as for dsf_mesolve (the library calls back
+    for every trajectory whose coherence changes).  Returns dict(expect[k, t],
+    traj_expect[j, k, t]?, shifts, stats)."""
+    import scipy.sparse as sp
+    lib = load()
+    mods = [sp.csr_matrix(a, dtype=np.complex128) for a in op_list]
+    dim = mods[0].shape[0]
+    eye = sp.identity(dim, dtype=np.complex128, format="csr")
+    n_e = len(e_fn(mods))
+    errors = []
+
+    def build(alpha_p, n_modes, user, out):
+        try:
+            al = [complex(alpha_p[k].re, alpha_p[k].im) for k in range(n_modes)]
+            ops = [a + x * eye for a, x in zip(mods, al)]
+            out[0] = system_create(H_fn(ops), c_fn(ops), e_fn(ops)).value
+            return QTL_OK
+        except Exception as ex:   # reported after the call
+            errors.append(ex)
+            return QTL_EINVAL
+
+    cb = DSF_BUILD(build)
+    holders = [_OpHolder(a) for a in mods]
+    ops_arr = (Op * len(mods))(*[h.op for h in holders])
+    a0 = np.ascontiguousarray(np.asarray(alpha0, dtype=np.complex128))
+    p0 = np.ascontiguousarray(psi0, dtype=np.complex128)
+    tl = np.ascontiguousarray(tlist, dtype=np.float64)
+    nt = len(tl)
+    ex = np.zeros((max(n_e, 1), nt), dtype=np.complex128)
+    tex = np.zeros((int(ntraj), max(n_e, 1), nt), dtype=np.complex128) if keep_trajectories else None
+    shifts = C.c_int64(0)
+    st = Stats()
+    status = lib.qtl_dsf_mcsolve(cb, None, len(mods), ops_arr, _ptr(a0), _ptr(p0), _ptr(tl), nt,
+                                 float(threshold), int(ntraj), C.c_uint64(int(seed) & (2**64 - 1)),
+                                 C.byref(make_opts(**kw)), n_e, _ptr(ex), _ptr(tex), C.byref(shifts),
+                                 C.byref(st))
+    if errors:
+        raise errors[0]
+    _check(status, "qtl_dsf_mcsolve")
+    out = dict(expect=ex[:n_e], shifts=int(shifts.value), stats=st.as_dict())
+    if keep_trajectories:
+        out["traj_expect"] = tex[:, :n_e]
+    return out
 
 
 class System:
