@@ -135,7 +135,7 @@ struct System {
 // -------------------------------------------- device-side solve descriptors
 struct MeJob {
     int n, L;
-    int n_td;             // time-dependent terms f_k(t) L_k (FP64 single solves)
+    int n_td;             // time-dependent terms f_k(t) L_k (single solves)
     const int32_t* trp;   // L_k = -i (I kron H_k - H_k^T kron I) stacked (rows k*L + r)
     const int32_t* tci;
     const double2* tv;
@@ -159,6 +159,7 @@ struct MeJob {
     int fixed;
     int method;
     int smem_nnz;         // per-CTA shared-memory capacity for Liouvillian entries
+    double2* tdg;         // mixed precision with n_td > 0: scratch [2][n_td][L], L_k y in FP64
 };
 
 // Time-dependent Hamiltonian terms f_k(t) H_k per system (qtl_system_add_td).

@@ -117,6 +117,12 @@ struct MeShared {
     int scan[ME_NW];
     double tnow;                   // the step's start (time-dependent terms)
     double2 tdf[7][QTL_MAX_TD];    // f_k at t + c_s h (slots 1..6) and at one other time (slot 0)
+    // mixed precision with time-dependent terms: f_k at the step's start, and
+    // phi[s][k] = h sum_{j<s} a_sj f_k(t_j) (s = 1..6; the stage inputs and
+    // y_new), phi[0][k] = h sum_j e_j f_k(t_j) (the error estimate)
+    double2 tdfs[QTL_MAX_TD];
+    double2 tdphi[7][QTL_MAX_TD];
+    float2 tdphif[7][QTL_MAX_TD];
 };
 
 // Row q of this CTA's cached Liouvillian times the stage input held in the
@@ -270,6 +276,34 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
         }
         return make_double2(rx, ry);
     };
+    // mixed precision: (L_k x)_r of one term k, x in the stage-input slots at
+    // boff as FP64 values or (f32) as FP32 values in the slots' first
+    // halves; FP64 sums
+    auto td_one = [&](int r, uint32_t boff, int q, bool f32) -> double2 {
+        double ax = 0.0, ay = 0.0;
+        const int rr = q * L + r;
+        for (int p = __ldg(J.trp + rr); p < __ldg(J.trp + rr + 1); ++p) {
+            const int c = __ldg(J.tci + p);
+            const double2 v = __ldg(J.tv + p);
+            const uint32_t slot_c = c_pow2 ? (uint32_t)(c >> c_lg) : (uint32_t)(c / C);
+            const uint32_t rank_c = c_pow2 ? (uint32_t)(c & (C - 1)) : (uint32_t)(c % C);
+            const uint32_t a = dsmem_map(ys_base + slot_c * (uint32_t)sizeof(double2), rank_c) + boff;
+            double2 x;
+            if (f32) {
+                const float2 xf = ld_dsmem(a, (float2*)nullptr);
+                x = make_double2((double)xf.x, (double)xf.y);
+            } else {
+                x = ld_dsmem(a, (double2*)nullptr);
+            }
+            ax += v.x * x.x - v.y * x.y;
+            ay += v.x * x.y + v.y * x.x;
+        }
+        return make_double2(ax, ay);
+    };
+    // mixed precision: g_k = L_k y of the current state y (FP64, buffer gb
+    // of J.tdg), row r
+    int gb = 0;
+    auto tdg_at = [&](int buf, int q, int r) -> double2* { return J.tdg + ((size_t)buf * J.n_td + q) * L + r; };
 
     double2 y[RPT], ynew[RPT];
     float2 yf[RPT], yfn[RPT];  // MIXED: FP32 copies, so the stage loop converts nothing
@@ -339,7 +373,10 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
         }
     }
     // time-dependent terms: f_k(tlist[0]) for k1 (slot 0)
-    if (warp == 0 && lane < J.n_td) sh.tdf[0][lane] = td_coef(J.tf[lane], J.tlist[0]);
+    if (warp == 0 && lane < J.n_td) {
+        sh.tdf[0][lane] = td_coef(J.tf[lane], J.tlist[0]);
+        sh.tdfs[lane] = sh.tdf[0][lane];
+    }
     cl.sync();
 
     // Per-CTA FP64 partials of Tr(O_e rho) over own rows -> J.epart[idx][rank][*].
@@ -431,6 +468,18 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
             k1d[m] = spmv_dsm64(tid + ME_T * m, s_seg, s_addr, J.lv64, gstart[m], 0u);
             k1f[m] = make_float2((float)k1d[m].x, (float)k1d[m].y);
             k[0][m] = k1f[m];
+            if (J.n_td > 0) {
+                // g_k = L_k y0 (FP64), and k[0] = L(t0) y0 for the starting step
+                double fx = k1d[m].x, fy = k1d[m].y;
+                for (int q = 0; q < J.n_td; ++q) {
+                    const double2 g = td_one(row[m], 0u, q, false);
+                    *tdg_at(0, q, row[m]) = g;
+                    const double2 f = sh.tdf[0][q];
+                    fx += f.x * g.x - f.y * g.y;
+                    fy += f.x * g.y + f.y * g.x;
+                }
+                k[0][m] = make_float2((float)fx, (float)fy);
+            }
         } else {
             k[0][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, 0u);
             if (J.n_td > 0) {
@@ -482,9 +531,10 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             if constexpr (MIXED) {
-                // increment form: f(y0 + h0 f0) - f0 = L (h0 f0)
+                // increment form: f(y0 + h0 f0) - f0 = L (h0 f0) (plus, with
+                // time-dependent terms, (f_k(t0 + h0) - f_k(t0)) L_k y0)
                 *slot_f(s_ys + RPT * ME_T, tid + ME_T * m) =
-                    make_float2((float)h0 * k1f[m].x, (float)h0 * k1f[m].y);
+                    make_float2((float)h0 * k[0][m].x, (float)h0 * k[0][m].y);
             } else {
                 const double2 f0 = to_d2(k[0][m]);
                 s_ys[RPT * ME_T + tid + ME_T * m] =
@@ -502,6 +552,19 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 const T2 c = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff);
                 dx = (float)c.x;
                 dy = (float)c.y;
+                if (J.n_td > 0) {
+                    double ex = 0.0, ey = 0.0;
+                    for (int q = 0; q < J.n_td; ++q) {
+                        const double2 f1 = sh.tdf[0][q], f0 = sh.tdfs[q];
+                        const double2 u = td_one(row[m], bufoff, q, true);
+                        const double2 g = *tdg_at(0, q, row[m]);
+                        const double dfx = f1.x - f0.x, dfy = f1.y - f0.y;
+                        ex += f1.x * u.x - f1.y * u.y + dfx * g.x - dfy * g.y;
+                        ey += f1.x * u.y + f1.y * u.x + dfx * g.y + dfy * g.x;
+                    }
+                    dx += (float)ex;
+                    dy += (float)ey;
+                }
             } else {
                 double2 f1 = to_d2(spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, bufoff));
                 if (J.n_td > 0) {
@@ -596,6 +659,26 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 const int st = 1 + i / J.n_td, q = i % J.n_td;
                 sh.tdf[st][q] = td_coef(J.tf[q], sh.tnow + tab.c[st] * hh);
             }
+            if constexpr (MIXED) {
+                if (J.n_td > 0) {
+                    // f_k at the step's start, then the sums over the stages
+                    if (lane < J.n_td) sh.tdfs[lane] = td_coef(J.tf[lane], sh.tnow);
+                    __syncwarp();
+                    for (int i = lane; i < 7 * J.n_td; i += 32) {
+                        const int st = i / J.n_td, q = i % J.n_td;
+                        double px = 0.0, py = 0.0;
+                        const int jn = st == 0 ? 7 : st;
+                        for (int j = 0; j < jn; ++j) {
+                            const double2 f = j == 0 ? sh.tdfs[q] : sh.tdf[j][q];
+                            const double w = st == 0 ? tab.e[j] : tab.a[st][j];
+                            px += w * f.x;
+                            py += w * f.y;
+                        }
+                        sh.tdphi[st][q] = make_double2(hh * px, hh * py);
+                        sh.tdphif[st][q] = make_float2((float)(hh * px), (float)(hh * py));
+                    }
+                }
+            }
         }
     };
     if (tid == 0) next_action();
@@ -647,10 +730,29 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                     if (s < 6) {
                         ax = fmaf(hc, k1f[m].x, ax);
                         ay = fmaf(hc, k1f[m].y, ay);
+                        if (J.n_td > 0 && own[m]) {
+                            // + sum_k phi[s][k] g_k (the stage times' f_k on L_k y)
+                            for (int q = 0; q < J.n_td; ++q) {
+                                const double2 gd = *tdg_at(gb, q, row[m]);
+                                const float2 g = make_float2((float)gd.x, (float)gd.y), ph = sh.tdphif[s][q];
+                                ax = fmaf(ph.x, g.x, fmaf(-ph.y, g.y, ax));
+                                ay = fmaf(ph.x, g.y, fmaf(ph.y, g.x, ay));
+                            }
+                        }
                         *slot_f(ysb, tid + ME_T * m) = make_float2(ax, ay);
                     } else {
                         ynew[m] = make_double2(fma(hcur, k1d[m].x, y[m].x) + (double)ax,
                                                fma(hcur, k1d[m].y, y[m].y) + (double)ay);
+                        if (J.n_td > 0 && own[m]) {
+                            double tx = 0.0, ty = 0.0;
+                            for (int q = 0; q < J.n_td; ++q) {
+                                const double2 g = *tdg_at(gb, q, row[m]), ph = sh.tdphi[6][q];
+                                tx += ph.x * g.x - ph.y * g.y;
+                                ty += ph.x * g.y + ph.y * g.x;
+                            }
+                            ynew[m].x += tx;
+                            ynew[m].y += ty;
+                        }
                         yfn[m] = make_float2((float)ynew[m].x, (float)ynew[m].y);
                         ysb[tid + ME_T * m] = ynew[m];
                     }
@@ -661,9 +763,33 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                     if (!own[m]) continue;
                     if (s < 6) {
                         k[s][m] = spmv_dsm<T2, TV>(tid + ME_T * m, s_seg, s_addr, s_v, off);
+                        if (J.n_td > 0) {
+                            // + sum_k f_k(t_s) L_k delta_s
+                            double ex = 0.0, ey = 0.0;
+                            for (int q = 0; q < J.n_td; ++q) {
+                                const double2 u = td_one(row[m], off, q, true), f = sh.tdf[s][q];
+                                ex += f.x * u.x - f.y * u.y;
+                                ey += f.x * u.y + f.y * u.x;
+                            }
+                            k[s][m].x += (float)ex;
+                            k[s][m].y += (float)ey;
+                        }
                     } else {
                         k7d[m] = spmv_dsm64(tid + ME_T * m, s_seg, s_addr, J.lv64, gstart[m], off);
-                        k[6][m] = make_float2((float)(k7d[m].x - k1d[m].x), (float)(k7d[m].y - k1d[m].y));
+                        double cx = k7d[m].x - k1d[m].x, cy = k7d[m].y - k1d[m].y;
+                        if (J.n_td > 0) {
+                            // g_k of y_new into the other buffer; the correction
+                            // k_7 - L(t + h) y = (L0 y_new - L0 y) + sum_k f_k(t + h) (g_k' - g_k)
+                            for (int q = 0; q < J.n_td; ++q) {
+                                const double2 g1 = td_one(row[m], off, q, false), g0 = *tdg_at(gb, q, row[m]);
+                                *tdg_at(gb ^ 1, q, row[m]) = g1;
+                                const double2 f = sh.tdf[6][q];
+                                const double dx = g1.x - g0.x, dy = g1.y - g0.y;
+                                cx += f.x * dx - f.y * dy;
+                                cy += f.x * dy + f.y * dx;
+                            }
+                        }
+                        k[6][m] = make_float2((float)cx, (float)cy);
                     }
                 }
             } else {
@@ -711,6 +837,15 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 for (int j = MIXED ? 1 : 0; j < 7; ++j) {
                     ex = fma(he[j], k[j][m].x, ex);
                     ey = fma(he[j], k[j][m].y, ey);
+                }
+                if constexpr (MIXED) {
+                    // the stage bases differ by sum_k f_k(t_j) g_k: + sum_k psi_k g_k
+                    for (int q = 0; q < J.n_td; ++q) {
+                        const double2 gd = *tdg_at(gb, q, row[m]);
+                        const float2 g = make_float2((float)gd.x, (float)gd.y), ps = sh.tdphif[0][q];
+                        ex = fmaf(ps.x, g.x, fmaf(-ps.y, g.y, ex));
+                        ey = fmaf(ps.x, g.y, fmaf(ps.y, g.x, ey));
+                    }
                 }
                 float yx, yy, nx, ny;
                 if constexpr (MIXED) {
@@ -778,6 +913,7 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                     k[0][m] = k[6][m];
                 }
             }
+            if constexpr (MIXED) gb ^= (J.n_td > 0);   // g_k of y_new
             if (land) states_write(sh.save_idx);
         }
     }

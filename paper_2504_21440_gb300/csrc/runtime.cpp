@@ -1318,8 +1318,8 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     if (s.n > 46340) return QTL_ETOOBIG;
     s.solved = true;
     if (!s.Htd.empty()) {
-        // time-dependent H: FP64 (cluster kernel when it fits, else the grid kernel)
-        if (opts->precision != QTL_FP64) return QTL_EINVAL;
+        // time-dependent H: the cluster kernel (FP64 or mixed) when it fits,
+        // else the grid kernel (FP64)
         if ((st = ensure_td_liouvillian(s)) != QTL_OK) return st;
     }
     {
@@ -1333,8 +1333,10 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
             me_plan((int)L64, opts->cluster_size, &C, &rpt);
             grid = cta_nnz_max_of(s, C) > me_smem_nnz_budget(opts->precision, rpt);
         }
-        if (grid)
+        if (grid) {
+            if (!s.Htd.empty() && opts->precision != QTL_FP64) return QTL_EINVAL;
             return mesolve_grid(s, state0_dev, is_ket, tlist_dev, nt, opts, expect_dev, states_dev, info_dev);
+        }
     }
     if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
@@ -1349,7 +1351,10 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     if (need > me_smem_nnz_budget(opts->precision, rpt)) return QTL_ETOOBIG;
     char* scratch = nullptr;
     const size_t epart_bytes = (size_t)nt * C * 2 * (s.n_e > 0 ? s.n_e : 1) * sizeof(double);
-    const size_t bytes = epart_bytes + sizeof(MeJob) + 512;
+    // mixed precision with time-dependent terms: L_k y of y and y_new (FP64)
+    const size_t tdg_bytes =
+        opts->precision == QTL_MIXED ? (size_t)2 * s.Htd.size() * (size_t)L * sizeof(double2) : 0;
+    const size_t bytes = epart_bytes + sizeof(MeJob) + 512 + tdg_bytes + 256;
     QTL_CUDA(qtl_malloc_async((void**)&scratch, bytes, stream));
     MeJob J;
     std::memset(&J, 0, sizeof(J));
@@ -1384,6 +1389,8 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     J.tci = s.dTL.ci;
     J.tv = s.dTL.v64;
     J.tf = s.d_tf;
+    if (tdg_bytes)
+        J.tdg = (double2*)(scratch + ((((epart_bytes + 255) & ~(size_t)255) + sizeof(MeJob) + 255) & ~(size_t)255));
     QTL_CUDA(cudaMemsetAsync(info_dev, 0, sizeof(qtl_device_info), stream));
     QTL_CUDA(cudaMemcpyAsync(jd, &J, sizeof(J), cudaMemcpyHostToDevice, stream));
     cudaError_t e = launch_me_cluster(jd, 1, L, J.smem_nnz, opts->precision, opts->cluster_size, nullptr, stream);

@@ -177,7 +177,7 @@ def test_time_dependent_systems_refuse_unsupported_paths():
     tl = np.linspace(0, 1, 3)
     g = qtl.System(H0, c_ops, e_ops, td=[(spec[0][0], spec[0][1])])
     with pytest.raises(qtl.QtlError) as e1:
-        g.mesolve(psi0, tl, precision="mixed")
+        g.mesolve(psi0, tl, precision="mixed", engine="grid")   # mixed: cluster kernel only
     with pytest.raises(qtl.QtlError) as e3:
         g.sesolve(psi0, tl)                      # has collapse operators
     g.mesolve(psi0, tl, fixed_dt=0.01)          # a solve ran: no more terms
@@ -211,3 +211,44 @@ def test_mcsolve_td_two_and_four_rows_per_thread(N):
         g.free()
     ref = mcsolve_td(H0, ot, c_ops, e_ops, psi0, tl, 3, 17, fixed_dt=0.01, keep_trajectories=True)
     assert maxabs(got["traj_expect"], ref["traj_expect"]) <= 1e-9
+
+
+@pytest.mark.parametrize("which", ["cos", "pair", "optomech"])
+def test_mesolve_td_mixed_precision_within_1e6_of_fp64(which):
+    """Mixed-precision mesolve with time-dependent terms (cluster kernel: the
+    increment form with one FP64 base product L_k y per term, the stage
+    times' f_k entering through per-stage sums) against the FP64 solve of
+    the same system on every expectation value, adaptively and at fixed
+    steps; the cos and pair cavities also against their closed forms."""
+    qtl = require_gpu()
+    if which == "optomech":
+        Nc, Nm = 10, 7
+        wc, wm, gc, kap, gam = 1.0, 2.0, 0.05, 0.01, 0.01
+        a = sp.kron(destroy(Nc), sp.identity(Nm), format="csr")
+        b = sp.kron(sp.identity(Nc), destroy(Nm), format="csr")
+        ad, bd = a.conj().T, b.conj().T
+        H0 = (wc * ad @ a + wm * bd @ b + gc / 2 * (a + ad) @ (a + ad) @ (b + bd)).tocsr()
+        spec = [((a + ad).tocsr(), dict(kind="cos", amp=10 * kap, omega=wc))]
+        c_ops = [math.sqrt(kap) * a, math.sqrt(gam) * b]
+        e_ops = [(ad @ a).tocsr(), a]
+        psi0 = np.zeros(Nc * Nm, dtype=complex)
+        psi0[0] = 1
+        tl = np.linspace(0, 20, 11)
+        alpha = None
+    else:
+        H0, spec, c_ops, e_ops, psi0, alpha = _cos_cavity() if which == "cos" else _pair_cavity()
+        tl = np.linspace(0, 8, 17)
+    _, lt = both(spec)
+    g = qtl.System(H0, c_ops, e_ops, td=lt)
+    try:
+        ref = g.mesolve(psi0, tl, rtol=1e-10, atol=1e-12, engine="cluster")
+        mix = g.mesolve(psi0, tl, precision="mixed", rtol=1e-7, atol=1e-9, engine="cluster")
+        fx64 = g.mesolve(psi0, tl, fixed_dt=0.01, engine="cluster")
+        fxm = g.mesolve(psi0, tl, fixed_dt=0.01, precision="mixed", engine="cluster")
+    finally:
+        g.free()
+    assert mix["stats"]["steps_acc"] > 10
+    assert maxabs(mix["expect"], ref["expect"]) <= 1e-6
+    assert maxabs(fxm["expect"], fx64["expect"]) <= 1e-6
+    if alpha is not None:
+        assert np.max(np.abs(mix["expect"][0] - alpha(tl))) <= 1e-6
