@@ -192,8 +192,10 @@ typedef struct {
  * kernel adds f_k(t) L_k y with L_k = -i (I kron H_k - H_k^T kron I); the
  * grid kernel adds f_k(t) ((-i H_k) rho + rho (i H_k)) and integrates only
  * the lower triangle of rho when H0 and every H_k are exactly Hermitian and
- * every f_k is real, QTL_COEF_COS with amp_im = 0).  Mixed-precision
- * mesolve, batches and plans return QTL_EINVAL for such a system.
+ * every f_k is real, QTL_COEF_COS with amp_im = 0), and in mixed precision
+ * on the cluster kernel (the products L_k y of each step's state in FP64,
+ * the stage increments' products in FP32).  Mixed-precision mesolve on the
+ * grid kernel, batches and plans return QTL_EINVAL for such a system.
  * Errors: QTL_EINVAL (NULL, bad operator or coefficient, 8 terms already,
  * n > 1024, a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
 qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f);
