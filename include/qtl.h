@@ -194,8 +194,9 @@ typedef struct {
  * the lower triangle of rho when H0 and every H_k are exactly Hermitian and
  * every f_k is real, QTL_COEF_COS with amp_im = 0), and in mixed precision
  * on the cluster kernel (the products L_k y of each step's state in FP64,
- * the stage increments' products in FP32).  Mixed-precision mesolve on the
- * grid kernel, batches and plans return QTL_EINVAL for such a system.
+ * the stage increments' products in FP32), also inside batches and batch
+ * plans.  Mixed-precision mesolve on the grid kernel returns QTL_EINVAL for
+ * such a system.
  * Errors: QTL_EINVAL (NULL, bad operator or coefficient, 8 terms already,
  * n > 1024, a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
 qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f);
@@ -249,6 +250,8 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
  * with the same plan share one launch (clusters take solves dynamically,
  * largest first); different plans run concurrently on streams forked from
  * opts->cuda_stream and joined back into it.  opts->cluster_size is ignored.
+ * Systems with time-dependent terms are taken, in FP64 and in mixed
+ * precision (scratch for their FP64 products L_k y is allocated per solve).
  *   _async: state0_dev[b], expect_dev[b] are device pointers held in host
  *   arrays of nb entries; is_ket[b] host array; info_dev a device array of nb
  *   qtl_device_info.  Host form: the same with host pointers, stats[b] (or

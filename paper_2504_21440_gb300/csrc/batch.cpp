@@ -96,9 +96,9 @@ extern "C" qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb,
     if (st != QTL_OK) return st;
     for (int b = 0; b < nb; ++b) {
         if (!systems[b] || !state0_dev[b] || (systems[b]->s.n_e > 0 && !expect_dev[b])) return QTL_EINVAL;
-        if (!systems[b]->s.Htd.empty()) return QTL_EINVAL;   // time-dependent H: not on the cluster kernel
         systems[b]->s.solved = true;
         if ((st = ensure_liouvillian(systems[b]->s)) != QTL_OK) return st;
+        if (!systems[b]->s.Htd.empty() && (st = ensure_td_liouvillian(systems[b]->s)) != QTL_OK) return st;
     }
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     qtl_batch* p = new qtl_batch();
@@ -174,10 +174,11 @@ extern "C" qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb,
             };
             const size_t o_tl = take(16), o_jobs = take((size_t)cnt * sizeof(MeJob)), o_cnt = take(sizeof(int)),
                          o_info = take((size_t)cnt * sizeof(qtl_device_info));
-            std::vector<size_t> o_ex(cnt), o_ep(cnt);
+            std::vector<size_t> o_ex(cnt), o_ep(cnt), o_td(cnt);
             for (int q = 0; q < cnt; ++q) {
                 o_ex[q] = take((size_t)ne_of(g[q]) * 2 * 16);
                 o_ep[q] = take((size_t)2 * 16 * 2 * ne_of(g[q]) * sizeof(double));
+                o_td[q] = take(me_tdg_bytes(systems[g[q]]->s, p->precision));
             }
             char* ps = nullptr;
             if (cudaMalloc((void**)&ps, off) != cudaSuccess) return fail(QTL_ENOMEM);
@@ -194,7 +195,8 @@ extern "C" qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb,
                 for (int q = 0; q < cnt; ++q)
                     me_job_fill(jobs[q], systems[g[q]]->s, (const double*)(ps + o_tl), 2, state0_dev[g[q]],
                                 is_ket[g[q]], (double*)(ps + o_ep[q]), (qtl_c128*)(ps + o_ex[q]),
-                                (qtl_device_info*)(ps + o_info) + q, opts, need);
+                                (qtl_device_info*)(ps + o_info) + q, opts, need,
+                                me_tdg_bytes(systems[g[q]]->s, p->precision) ? (double2*)(ps + o_td[q]) : nullptr);
                 ok = cudaMemcpy(ps + o_jobs, jobs.data(), (size_t)cnt * sizeof(MeJob), cudaMemcpyHostToDevice) ==
                      cudaSuccess;
                 float ms = 0.f;
@@ -235,9 +237,12 @@ extern "C" qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb,
         return o;
     };
     const size_t o_jobs = take((size_t)nb * sizeof(MeJob)), o_cnt = take((size_t)ng * sizeof(int));
-    std::vector<size_t> o_ep(nb);
+    std::vector<size_t> o_ep(nb), o_td(nb);
     for (int k = 0; k < ng; ++k)
-        for (int b : p->group[k]) o_ep[b] = take((size_t)nt * p->C[k] * 2 * ne_of(b) * sizeof(double));
+        for (int b : p->group[k]) {
+            o_ep[b] = take((size_t)nt * p->C[k] * 2 * ne_of(b) * sizeof(double));
+            o_td[b] = take(me_tdg_bytes(systems[b]->s, p->precision));
+        }
     if (cudaMalloc((void**)&p->scratch, off) != cudaSuccess) return fail(QTL_ENOMEM);
     p->jobs = (MeJob*)(p->scratch + o_jobs);
     p->counters = (int*)(p->scratch + o_cnt);
@@ -246,7 +251,8 @@ extern "C" qtl_status qtl_batch_create(qtl_system* const* systems, int32_t nb,
     for (int k = 0; k < ng; ++k)
         for (int b : p->group[k])
             me_job_fill(jobs[q++], systems[b]->s, tlist_dev, nt, state0_dev[b], is_ket[b],
-                        (double*)(p->scratch + o_ep[b]), expect_dev[b], info_dev + b, opts, p->smem[k]);
+                        (double*)(p->scratch + o_ep[b]), expect_dev[b], info_dev + b, opts, p->smem[k],
+                        me_tdg_bytes(systems[b]->s, p->precision) ? (double2*)(p->scratch + o_td[b]) : nullptr);
     if (cudaMemcpy(p->jobs, jobs.data(), (size_t)nb * sizeof(MeJob), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(QTL_ECUDA);
 

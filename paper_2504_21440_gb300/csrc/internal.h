@@ -342,9 +342,15 @@ qtl_status ensure_liouvillian(System& s, int64_t max_rows = -1);
 qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu = nullptr);
 void batch_plan(int L, int* C, int* rpt);
 int64_t cta_nnz_max(const System& s, int C);
+// one cluster-kernel job; tdg: scratch of 2 n_td n^2 complex (mixed
+// precision with time-dependent terms), else null
 void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, const qtl_c128* state0_dev,
                  int is_ket, double* epart, qtl_c128* expect_dev, qtl_device_info* info_dev,
-                 const qtl_opts* opts, int smem_nnz);
+                 const qtl_opts* opts, int smem_nnz, double2* tdg = nullptr);
+// bytes of that scratch for a solve of s in the given precision (0 if none)
+size_t me_tdg_bytes(const System& s, int precision);
+// the Liouvillians of the time-dependent terms on the device (built once)
+qtl_status ensure_td_liouvillian(System& s);
 
 // Stream-ordered allocation from the library's own pool on the current
 // device.  The pool keeps up to 16 GiB of freed memory for reuse instead

@@ -645,7 +645,7 @@ static qtl_status ensure_grid(System& s) {
 // The Liouvillians of the time-dependent terms alone, L_k = -i (I kron H_k -
 // H_k^T kron I) (column stacking: row i + n j holds -i H_k[i][l] at column
 // l + n j and +i H_k[l][j] at column i + n l), stacked row-wise.
-static qtl_status ensure_td_liouvillian(System& s) {
+qtl_status ensure_td_liouvillian(System& s) {
     std::lock_guard<std::mutex> lk(g_build_mu);
     if (s.Htd.empty() || s.dTL.rp) return QTL_OK;
     const int n = s.n;
@@ -899,9 +899,13 @@ int64_t cta_nnz_max(const System& s, int C) {
 }
 
 // One cluster-kernel job: system s from state0 over tlist with opts.
+size_t me_tdg_bytes(const System& s, int precision) {
+    return precision == QTL_MIXED ? (size_t)2 * s.Htd.size() * (size_t)s.n * s.n * sizeof(double2) : 0;
+}
+
 void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, const qtl_c128* state0_dev,
                  int is_ket, double* epart, qtl_c128* expect_dev, qtl_device_info* info_dev,
-                 const qtl_opts* opts, int smem_nnz) {
+                 const qtl_opts* opts, int smem_nnz, double2* tdg) {
     std::memset(&J, 0, sizeof(J));
     J.n = s.n;
     J.L = s.n * s.n;
@@ -928,6 +932,12 @@ void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, con
     J.fixed = opts->fixed_step ? 1 : 0;
     J.method = opts->method;
     J.smem_nnz = smem_nnz;
+    J.n_td = (int)s.Htd.size();
+    J.trp = s.dTL.rp;
+    J.tci = s.dTL.ci;
+    J.tv = s.dTL.v64;
+    J.tf = s.d_tf;
+    J.tdg = tdg;
 }
 
 }  // namespace qtl
@@ -1443,10 +1453,10 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
     std::vector<Plan> plan(nb);
     for (int b = 0; b < nb; ++b) {
         if (!systems[b] || !state0_dev[b] || (systems[b]->s.n_e > 0 && !expect_dev[b])) return QTL_EINVAL;
-        if (!systems[b]->s.Htd.empty()) return QTL_EINVAL;   // time-dependent H: not on the cluster kernel
         System& s = systems[b]->s;
         s.solved = true;
         if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+        if (!s.Htd.empty() && (st = ensure_td_liouvillian(s)) != QTL_OK) return st;
         const int L = s.n * s.n;
         batch_plan(L, &plan[b].C, &plan[b].rpt);
         plan[b].need = cta_nnz_max(s, plan[b].C);
@@ -1468,7 +1478,7 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
             return systems[x]->s.dL.nnz > systems[y]->s.dL.nnz;
         });
     // scratch: jobs (bucket order), per-job expectation partials, counters
-    std::vector<size_t> ep_off(nb);
+    std::vector<size_t> ep_off(nb), tdg_off(nb);
     size_t off = ((size_t)nb * sizeof(MeJob) + 255) & ~(size_t)255;
     const size_t cnt_off = off;
     off += ((size_t)nk * sizeof(int) + 255) & ~(size_t)255;
@@ -1476,6 +1486,8 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
         ep_off[b] = off;
         const int ne = systems[b]->s.n_e > 0 ? systems[b]->s.n_e : 1;
         off += (((size_t)nt * plan[b].C * 2 * ne * sizeof(double)) + 255) & ~(size_t)255;
+        tdg_off[b] = off;
+        off += (me_tdg_bytes(systems[b]->s, opts->precision) + 255) & ~(size_t)255;
     }
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     char* scratch = nullptr;
@@ -1487,7 +1499,8 @@ extern "C" qtl_status qtl_mesolve_batch_async(qtl_system* const* systems, int32_
         first[k] = q;
         for (int b : bucket[k])
             me_job_fill(jobs[q++], systems[b]->s, tlist_dev, nt, state0_dev[b], is_ket[b],
-                        (double*)(scratch + ep_off[b]), expect_dev[b], info_dev + b, opts, 0);
+                        (double*)(scratch + ep_off[b]), expect_dev[b], info_dev + b, opts, 0,
+                        me_tdg_bytes(systems[b]->s, opts->precision) ? (double2*)(scratch + tdg_off[b]) : nullptr);
     }
     first[nk] = q;
     for (int k = 0; k < nk; ++k) {
