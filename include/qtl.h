@@ -184,10 +184,11 @@ typedef struct {
 } qtl_coef;
 
 /* Adds the term f(t) Hk to the system's Hamiltonian (H of qtl_system_create
- * becomes H0).  Up to 8 terms; Hk has the system's dimension n <= 1024.
+ * becomes H0).  Up to 8 terms; Hk has the system's dimension.
  * Terms must be added before the system's first solve (QTL_EINVAL after).
  * Which solvers take them: qtl_sesolve and qtl_mcsolve (trajectories with
- * n <= 1024, FP64 or mixed precision: A(t) = A - i sum_k f_k(t) H_k), and
+ * n <= 1024, FP64 or mixed precision: A(t) = A - i sum_k f_k(t) H_k; above
+ * that QTL_EINVAL), and
  * qtl_mesolve / qtl_mesolve_async in FP64 on either engine (the cluster
  * kernel adds f_k(t) L_k y with L_k = -i (I kron H_k - H_k^T kron I); the
  * grid kernel adds f_k(t) ((-i H_k) rho + rho (i H_k)) and integrates only
@@ -198,7 +199,7 @@ typedef struct {
  * plans.  Mixed-precision mesolve on the grid kernel returns QTL_EINVAL for
  * such a system.
  * Errors: QTL_EINVAL (NULL, bad operator or coefficient, 8 terms already,
- * n > 1024, a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
+ * a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
 qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f);
 
 /* Releases the system and its device memory (NULL is a no-op).  Work enqueued

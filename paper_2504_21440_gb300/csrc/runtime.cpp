@@ -572,12 +572,6 @@ static qtl_status ensure_grid(System& s) {
     if (s.units) return QTL_OK;
     if ((st = upload_sell(s.Bt, s.sBt)) != QTL_OK) {
         free_sell(s.sBt);
-    for (DevSell& d : s.sTa) free_sell(d);
-    for (DevSell& d : s.sTb) free_sell(d);
-    free_csr(s.dT);
-    free_csr(s.dTL);
-    cudaFree(s.d_tf);
-    cudaFree(s.d_tsl);
         return st;
     }
     const int n = s.n, ns = (n + 31) / 32, ncg = (n + 3) / 4;
@@ -765,7 +759,6 @@ qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu)
     }
     if (s.n > 46340) return QTL_ETOOBIG;
     qtl_status st;
-    if (!s.Htd.empty() && (st = ensure_td_liouvillian(s)) != QTL_OK) return st;
     const int64_t L64 = (int64_t)s.n * s.n;
     bool grid = o->engine == QTL_ENGINE_GRID || (o->engine == QTL_ENGINE_AUTO && L64 > me_cluster_capacity());
     if (!grid) {
@@ -777,6 +770,8 @@ qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu)
         }
     }
     if (fills_gpu) *fills_gpu = grid;
+    // time-dependent terms: their Liouvillians only for the cluster kernel
+    if (!grid && !s.Htd.empty() && (st = ensure_td_liouvillian(s)) != QTL_OK) return st;
     return grid ? ensure_grid(s) : QTL_OK;
 }
 
@@ -998,6 +993,14 @@ void qtl_system_free(qtl_system* sys) {
     cudaFree(s.units);
     cudaFree(s.odiag);
     cudaFree(s.ew);
+    // time-dependent terms: the trajectory kernel's stacked -i H_k, the
+    // cluster kernel's Liouvillians, the grid kernel's copies, coefficients
+    for (DevSell& d : s.sTa) free_sell(d);
+    for (DevSell& d : s.sTb) free_sell(d);
+    free_csr(s.dT);
+    free_csr(s.dTL);
+    cudaFree(s.d_tf);
+    cudaFree(s.d_tsl);
     ss_cache_free(s);
     delete sys;
 }
@@ -1087,7 +1090,7 @@ qtl_status qtl_system_create(const qtl_op* H, const qtl_op* c_ops, int32_t n_c, 
 qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f) {
     if (!sys || !Hk || !f) return QTL_EINVAL;
     System& s = sys->s;
-    if (s.solved || (int)s.Htd.size() >= QTL_MAX_TD || s.n > 1024) return QTL_EINVAL;
+    if (s.solved || (int)s.Htd.size() >= QTL_MAX_TD) return QTL_EINVAL;
     if (f->kind != QTL_COEF_COS && f->kind != QTL_COEF_EXP) return QTL_EINVAL;
     for (double v : {f->amp_re, f->amp_im, f->omega, f->phi, f->t0, f->sigma})
         if (!std::isfinite(v)) return QTL_EINVAL;
@@ -1327,12 +1330,9 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
     System& s = sys->s;
     if (s.n > 46340) return QTL_ETOOBIG;
     s.solved = true;
-    if (!s.Htd.empty()) {
+    {
         // time-dependent H: the cluster kernel (FP64 or mixed) when it fits,
         // else the grid kernel (FP64)
-        if ((st = ensure_td_liouvillian(s)) != QTL_OK) return st;
-    }
-    {
         // engine: the cluster kernel when the problem fits one cluster
         const int64_t L64 = (int64_t)s.n * s.n;
         bool grid = opts->engine == QTL_ENGINE_GRID ||
@@ -1349,6 +1349,7 @@ qtl_status qtl_mesolve_async(qtl_system* sys, const qtl_c128* state0_dev, int32_
         }
     }
     if ((st = ensure_liouvillian(s)) != QTL_OK) return st;
+    if (!s.Htd.empty() && (st = ensure_td_liouvillian(s)) != QTL_OK) return st;
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     const int L = s.n * s.n;
     // Largest number of Liouvillian entries in one CTA's rows (CTA c owns the

@@ -286,3 +286,23 @@ def test_mesolve_td_mixed_precision_within_1e6_of_fp64(which):
     assert maxabs(fxm["expect"], fx64["expect"]) <= 1e-6
     if alpha is not None:
         assert np.max(np.abs(mix["expect"][0] - alpha(tl))) <= 1e-6
+
+
+def test_mesolve_td_beyond_n_1024_on_the_grid_kernel():
+    """A cos-driven damped cavity at N = 1100 (rho with 1.21M entries): the
+    FP64 grid mesolve against the closed form of its coherent amplitude;
+    trajectories refuse the system (the wide trajectory kernel takes no
+    time-dependent terms) and so does sesolve (n <= 1024)."""
+    qtl = require_gpu()
+    H0, spec, c_ops, e_ops, psi0, alpha = _cos_cavity(N=1100)
+    _, lt = both(spec)
+    tl = np.linspace(0, 4, 9)
+    g = qtl.System(H0, c_ops, e_ops, td=lt)
+    try:
+        r = g.mesolve(psi0, tl, rtol=1e-10, atol=1e-12)
+        assert np.max(np.abs(r["expect"][0] - alpha(tl))) <= 1e-8
+        with pytest.raises(qtl.QtlError) as e:
+            g.mcsolve(psi0, tl, 4, 1)
+        assert e.value.status == qtl.QTL_EINVAL
+    finally:
+        g.free()
