@@ -186,9 +186,9 @@ typedef struct {
 /* Adds the term f(t) Hk to the system's Hamiltonian (H of qtl_system_create
  * becomes H0).  Up to 8 terms; Hk has the system's dimension.
  * Terms must be added before the system's first solve (QTL_EINVAL after).
- * Which solvers take them: qtl_sesolve and qtl_mcsolve (trajectories with
- * n <= 1024, FP64 or mixed precision: A(t) = A - i sum_k f_k(t) H_k; above
- * that QTL_EINVAL), and
+ * Which solvers take them: qtl_sesolve (n <= 1024) and qtl_mcsolve
+ * (trajectories, A(t) = A - i sum_k f_k(t) H_k: FP64 or mixed precision up to
+ * n = 1024, FP64 above, where mixed precision returns QTL_EINVAL), and
  * qtl_mesolve / qtl_mesolve_async in FP64 on either engine (the cluster
  * kernel adds f_k(t) L_k y with L_k = -i (I kron H_k - H_k^T kron I); the
  * grid kernel adds f_k(t) ((-i H_k) rho + rho (i H_k)) and integrates only

@@ -258,6 +258,7 @@ struct McJob {
     const double2* tv64;
     const float2* tv32;
     const qtl_coef* tf;   // device [n_td] coefficients
+    const SellRef* tsl;   // wide trajectory kernel (FP64): -i H_k in sliced ELLPACK, [n_td]
     const double* tlist;
     int nt;
     const double2* psi0;
@@ -351,6 +352,8 @@ void me_job_fill(MeJob& J, const System& s, const double* tlist_dev, int nt, con
 size_t me_tdg_bytes(const System& s, int precision);
 // the Liouvillians of the time-dependent terms on the device (built once)
 qtl_status ensure_td_liouvillian(System& s);
+// the time-dependent terms in sliced ELLPACK (s.sTa, s.sTb, s.d_tsl; built once)
+qtl_status ensure_td_sell(System& s);
 
 // Stream-ordered allocation from the library's own pool on the current
 // device.  The pool keeps up to 16 GiB of freed memory for reuse instead

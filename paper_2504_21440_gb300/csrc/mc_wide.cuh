@@ -442,6 +442,27 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
     auto rhs_row = [&](int r, const T2* x) -> T2 {
         return sell_row<MIXED, T, T2, IT, XS, DC>(r, J.sl, J.sdesc, C, (const IT*)J.sci, svs, svc, x, pol);
     };
+    // FP64: A x plus sum_k f_k (-i H_k x) with the coefficients of slot `slot`
+    // (1..6: the stages of the current step, 7: one other time); the
+    // mixed-precision kernel takes no time-dependent terms
+    auto rhs_td = [&](int r, const T2* x, int slot) -> T2 {
+        T2 v = rhs_row(r, x);
+        if constexpr (!MIXED) {
+            for (int k = 0; k < J.n_td; ++k) {
+                const SellRef R = J.tsl[k];
+                const T2 w = sell_row<false, double, double2, int32_t, XS, false>(r, R.sl, R.desc, C, R.ci, R.vs64,
+                                                                                 R.vc64, x, pol);
+                const double2 f = cb.tdf[slot][k];
+                v.x += f.x * w.x - f.y * w.y;
+                v.y += f.x * w.y + f.y * w.x;
+            }
+        }
+        return v;
+    };
+    // warp 0: f_k at time tp into slot 7
+    auto publish_td_at = [&](double tp) {
+        if (lane < J.n_td) cb.tdf[7][lane] = td_coef(J.tf[lane], tp);
+    };
     // mixed precision: f = A (X + XL) for every row into slot `role` (pair)
     auto base_deriv = [&](int role, const T2* xh) {
         if constexpr (MIXED) {
@@ -514,11 +535,13 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
             X0[q] = o;
             if constexpr (MIXED) XL[q] = lo_of(v, o);
         }
+        if constexpr (!MIXED)
+            if (warp == 0 && J.n_td > 0) publish_td_at(J.tlist[0]);
         __syncthreads();
         if constexpr (MIXED)
             base_deriv(0, X0);
         else
-            for (int q = tid; q < n; q += MW_T) Kp(0)[q] = rhs_row(q, X0);
+            for (int q = tid; q < n; q += MW_T) Kp(0)[q] = rhs_td(q, X0, 7);
         __syncthreads();
 
         // <psi|O_e|psi>/<psi|psi> for psi = Y[ys] (written and synchronised by
@@ -625,11 +648,13 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                 const double2 f0 = k1_of(q);
                 X1[q] = from_d2_mc<T2>(make_double2(y.x + h0 * f0.x, y.y + h0 * f0.y));
             }
+            if constexpr (!MIXED)
+                if (warp == 0 && J.n_td > 0) publish_td_at(J.tlist[0] + h0);
             __syncthreads();
             double s2 = 0.0;
             for (int q = tid; q < n; q += MW_T) {
                 const double2 y = Yp(ys)[q];
-                const double2 f1 = to_d2_mc(rhs_row(q, X1));
+                const double2 f1 = to_d2_mc(rhs_td(q, X1, 7));
                 const double2 f0 = k1_of(q);
                 const float sc = (float)J.atol + (float)J.rtol * sqrtf((float)(y.x * y.x + y.y * y.y));
                 const float dx = (float)(f1.x - f0.x), dy = (float)(f1.y - f0.y);
@@ -646,6 +671,7 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
 
         auto next_action = [&]() {
             cb.pub = 0;
+            if constexpr (!MIXED) cb.tnow = t;
             for (;;) {
                 if (status != QTL_OK || idx >= J.nt) {
                     cb.action = MC_DONE;
@@ -696,6 +722,13 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                 if (lane < 28) {
                     cb.coef[lane] = c;
                     cb.coeff[lane] = (float)c;
+                }
+                // time-dependent terms (FP64): f_k at the stage times t + c_s htry
+                if constexpr (!MIXED) {
+                    for (int i = lane; i < 6 * J.n_td; i += 32) {
+                        const int st = 1 + i / J.n_td, qk = i % J.n_td;
+                        cb.tdf[st][qk] = td_coef(J.tf[qk], cb.tnow + tab.c[st] * hh);
+                    }
                 }
                 if constexpr (MIXED) {
                     if (lane >= 28) {
@@ -907,12 +940,12 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                 T2* ks = Kp(s);
                 if (s < 6) {
 #pragma unroll 2
-                    for (int q = tid; q < n; q += MW_T) __stcs(ks + q, rhs_row(q, xb));
+                    for (int q = tid; q < n; q += MW_T) __stcs(ks + q, rhs_td(q, xb, s));
                 } else {
                     const T he6 = coefT(27);
 #pragma unroll 2
                     for (int q = tid; q < n; q += MW_T) {
-                        const T2 kv = rhs_row(q, xb);
+                        const T2 kv = rhs_td(q, xb, 6);
                         __stcs(ks + q, kv);
                         const T2 ep = __ldcs(EP + q);
                         const float fx = (float)fma(he6, kv.x, ep.x);
@@ -1131,12 +1164,14 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                     n2p += nv.x * nv.x + nv.y * nv.y;
                 }
             }
+            if constexpr (!MIXED)
+                if (warp == 0 && J.n_td > 0) publish_td_at(cb.tnow);   // the time after the jump
             __syncthreads();
             if constexpr (MIXED) {
                 base_deriv(ys, X0);
             } else {
                 T2* k0 = Kp(0);
-                for (int q = tid; q < n; q += MW_T) k0[q] = rhs_row(q, X0);
+                for (int q = tid; q < n; q += MW_T) k0[q] = rhs_td(q, X0, 7);
             }
             {
                 float dummy = 0.f;

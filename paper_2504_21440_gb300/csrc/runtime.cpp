@@ -560,37 +560,14 @@ static bool exactly_hermitian(const Csr& m) {
     return true;
 }
 
-// Everything the grid mesolve kernel reads besides the CSR operators: A and
-// B^T in sliced ELLPACK, the warp work units and the two structure flags.
-// Units {row slice s, column group c} (32 rows x 4 columns) are ordered by
-// column group, then slice; those that meet the lower triangle (some row >=
-// some column) come first, so the Hermitian mode runs the first nu_tri.
-static qtl_status ensure_grid(System& s) {
-    qtl_status st = ensure_sell(s);
-    if (st != QTL_OK) return st;
-    std::lock_guard<std::mutex> lk(g_build_mu);
-    if (s.units) return QTL_OK;
-    if ((st = upload_sell(s.Bt, s.sBt)) != QTL_OK) {
-        free_sell(s.sBt);
-        return st;
-    }
-    const int n = s.n, ns = (n + 31) / 32, ncg = (n + 3) / 4;
-    std::vector<int2> lower, upper;
-    for (int c = 0; c < ncg; ++c)
-        for (int sl = 0; sl < ns; ++sl) {
-            const int amax = std::min(32 * sl + 31, n - 1);
-            (amax >= 4 * c ? lower : upper).push_back(make_int2(sl, c));
-        }
-    s.nu_tri = (int)lower.size();
-    s.nu_all = (int)(lower.size() + upper.size());
-    lower.insert(lower.end(), upper.begin(), upper.end());
-    if ((st = upload(&s.units, lower.data(), lower.size())) != QTL_OK) return st;
-    bool herm = exactly_hermitian(s.H);
-    for (size_t k = 0; k < s.Htd.size(); ++k)
-        herm = herm && s.ftd[k].kind == QTL_COEF_COS && s.ftd[k].amp_im == 0.0 && exactly_hermitian(s.Htd[k]);
-    s.herm_h = herm ? 1 : 0;
-    if (!s.Htd.empty()) {
-        // -i H_k and (i H_k)^T in sliced ELLPACK, and their references on the device
+// The time-dependent terms in sliced ELLPACK: -i H_k (the grid mesolve's
+// left factors and the wide trajectory kernel's products) and (i H_k)^T (the
+// grid's right factors), with their references on the device; built once.
+// The caller holds g_build_mu.
+static qtl_status ensure_td_sell_locked(System& s) {
+    if (s.Htd.empty() || s.d_tsl) return QTL_OK;
+    qtl_status st;
+    {
         const int ntd = (int)s.Htd.size();
         s.sTa.resize(ntd);
         s.sTb.resize(ntd);
@@ -629,6 +606,44 @@ static qtl_status ensure_grid(System& s) {
         }
         if ((st = upload(&s.d_tsl, refs.data(), refs.size())) != QTL_OK) return st;
     }
+    return QTL_OK;
+}
+
+qtl_status ensure_td_sell(System& s) {
+    std::lock_guard<std::mutex> lk(g_build_mu);
+    return ensure_td_sell_locked(s);
+}
+
+// Everything the grid mesolve kernel reads besides the CSR operators: A and
+// B^T in sliced ELLPACK, the warp work units and the two structure flags.
+// Units {row slice s, column group c} (32 rows x 4 columns) are ordered by
+// column group, then slice; those that meet the lower triangle (some row >=
+// some column) come first, so the Hermitian mode runs the first nu_tri.
+static qtl_status ensure_grid(System& s) {
+    qtl_status st = ensure_sell(s);
+    if (st != QTL_OK) return st;
+    std::lock_guard<std::mutex> lk(g_build_mu);
+    if (s.units) return QTL_OK;
+    if ((st = upload_sell(s.Bt, s.sBt)) != QTL_OK) {
+        free_sell(s.sBt);
+        return st;
+    }
+    const int n = s.n, ns = (n + 31) / 32, ncg = (n + 3) / 4;
+    std::vector<int2> lower, upper;
+    for (int c = 0; c < ncg; ++c)
+        for (int sl = 0; sl < ns; ++sl) {
+            const int amax = std::min(32 * sl + 31, n - 1);
+            (amax >= 4 * c ? lower : upper).push_back(make_int2(sl, c));
+        }
+    s.nu_tri = (int)lower.size();
+    s.nu_all = (int)(lower.size() + upper.size());
+    lower.insert(lower.end(), upper.begin(), upper.end());
+    if ((st = upload(&s.units, lower.data(), lower.size())) != QTL_OK) return st;
+    bool herm = exactly_hermitian(s.H);
+    for (size_t k = 0; k < s.Htd.size(); ++k)
+        herm = herm && s.ftd[k].kind == QTL_COEF_COS && s.ftd[k].amp_im == 0.0 && exactly_hermitian(s.Htd[k]);
+    s.herm_h = herm ? 1 : 0;
+    if ((st = ensure_td_sell_locked(s)) != QTL_OK) return st;
     bool real = true;
     for (const Csr& c : s.C)
         for (double v : c.im) real = real && v == 0.0;
@@ -755,7 +770,9 @@ qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu)
     if (kind == QTL_REQ_MCSOLVE) {
         const bool wide = s.n > mc_traj_capacity() || o->engine == QTL_ENGINE_GRID;
         if (fills_gpu) *fills_gpu = wide;
-        return wide ? ensure_sell(s) : QTL_OK;
+        if (!wide) return QTL_OK;
+        qtl_status st = ensure_sell(s);
+        return st == QTL_OK ? ensure_td_sell(s) : st;
     }
     if (s.n > 46340) return QTL_ETOOBIG;
     qtl_status st;
@@ -1703,7 +1720,8 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     if (s.n > mc_wide_capacity()) return QTL_ETOOBIG;
     if (opts->engine == QTL_ENGINE_CLUSTER && s.n > mc_traj_capacity()) return QTL_ETOOBIG;
     const bool wide = s.n > mc_traj_capacity() || opts->engine == QTL_ENGINE_GRID;
-    if (wide && !s.Htd.empty()) return QTL_EINVAL;   // time-dependent terms: trajectory kernel only
+    // time-dependent terms above the register-resident size: FP64 only
+    if (wide && !s.Htd.empty() && opts->precision != QTL_FP64) return QTL_EINVAL;
     s.solved = true;
     cudaStream_t stream = (cudaStream_t)opts->cuda_stream;
     const size_t ne = (size_t)s.n_e * nt;
@@ -1757,10 +1775,11 @@ qtl_status qtl_mcsolve_async(qtl_system* sys, const qtl_c128* psi0_dev, const do
     cudaError_t e = cudaSuccess;
     if (wide) {
         // per-CTA integrator state in global memory (psi does not fit on chip)
-        if ((st = ensure_sell(s)) != QTL_OK) {
+        if ((st = ensure_sell(s)) != QTL_OK || (st = ensure_td_sell(s)) != QTL_OK) {
             if (scratch) cudaFreeAsync(scratch, stream);
             return st;
         }
+        J.tsl = s.d_tsl;
         J.sl = s.sA.sl;
         J.sdesc = s.sA.desc;
         SellConst cdesc;

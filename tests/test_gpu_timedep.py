@@ -288,11 +288,12 @@ def test_mesolve_td_mixed_precision_within_1e6_of_fp64(which):
         assert np.max(np.abs(mix["expect"][0] - alpha(tl))) <= 1e-6
 
 
-def test_mesolve_td_beyond_n_1024_on_the_grid_kernel():
-    """A cos-driven damped cavity at N = 1100 (rho with 1.21M entries): the
-    FP64 grid mesolve against the closed form of its coherent amplitude;
-    trajectories refuse the system (the wide trajectory kernel takes no
-    time-dependent terms) and so does sesolve (n <= 1024)."""
+def test_td_beyond_n_1024_grid_mesolve_and_wide_trajectories():
+    """A cos-driven damped cavity at N = 1100 (rho with 1.21M entries; kets
+    above the register-resident size): the FP64 grid mesolve and every FP64
+    trajectory of the wide kernel against the closed form of the coherent
+    amplitude; mixed-precision trajectories of that size refuse the
+    time-dependent system."""
     qtl = require_gpu()
     H0, spec, c_ops, e_ops, psi0, alpha = _cos_cavity(N=1100)
     _, lt = both(spec)
@@ -301,8 +302,31 @@ def test_mesolve_td_beyond_n_1024_on_the_grid_kernel():
     try:
         r = g.mesolve(psi0, tl, rtol=1e-10, atol=1e-12)
         assert np.max(np.abs(r["expect"][0] - alpha(tl))) <= 1e-8
+        m = g.mcsolve(psi0, tl, 6, 2, keep_trajectories=True, rtol=1e-9, atol=1e-11)
+        assert np.max(np.abs(m["traj_expect"][:, 0, :] - alpha(tl)[None, :])) <= 1e-7
+        assert m["stats"]["jumps"] > 0
         with pytest.raises(qtl.QtlError) as e:
-            g.mcsolve(psi0, tl, 4, 1)
+            g.mcsolve(psi0, tl, 4, 1, precision="mixed")
         assert e.value.status == qtl.QTL_EINVAL
     finally:
         g.free()
+
+
+def test_td_wide_trajectory_kernel_equals_the_register_kernel():
+    """The exp-pair-driven cavity (N = 16) on the wide trajectory kernel
+    (engine="grid") and on the register-resident one, FP64 at fixed steps,
+    trajectory by trajectory, and against the oracle."""
+    qtl = require_gpu()
+    H0, spec, c_ops, e_ops, psi0, alpha = _pair_cavity()
+    ot, lt = both(spec)
+    tl = np.linspace(0, 4, 9)
+    g = qtl.System(H0, c_ops, e_ops, td=lt)
+    try:
+        wide = g.mcsolve(psi0, tl, 6, 5, keep_trajectories=True, fixed_dt=0.01, engine="grid")
+        reg = g.mcsolve(psi0, tl, 6, 5, keep_trajectories=True, fixed_dt=0.01, engine="cluster")
+    finally:
+        g.free()
+    ref = mcsolve_td(H0, ot, c_ops, e_ops, psi0, tl, 6, 5, fixed_dt=0.01, keep_trajectories=True)
+    assert maxabs(wide["traj_expect"], reg["traj_expect"]) <= 1e-10
+    assert maxabs(wide["traj_expect"], ref["traj_expect"]) <= 1e-9
+    assert wide["stats"]["jumps"] == reg["stats"]["jumps"] == ref["stats"]["jumps"] > 0
