@@ -490,8 +490,14 @@ qtl_status qtl_dsf_mesolve(qtl_dsf_build_fn build, void* user, int32_t n_modes, 
  * d_k = <psi|a_k|psi>/<psi|psi> of each trajectory and, when |d_k| >
  * threshold, psi <- exp(-d_k a_k^H + conj(d_k) a_k) psi (in the truncated
  * space, on the device), alpha_k^(j) += d_k, and the trajectory's system is
- * rebuilt by build (as for qtl_dsf_mesolve; until its first displacement a
- * trajectory uses the system built for alpha0).
+ * rebuilt (as for qtl_dsf_mesolve; until its first displacement a
+ * trajectory uses the system built for alpha0).  Rebuilds run on the device:
+ * at set-up the library calls build at sample frames and fits every entry of
+ * the operators as a polynomial of degree <= 6 in alpha_k and conj(alpha_k),
+ * accepted when it reproduces build at further frames to 1e-10 of the
+ * largest entry (refitted over a wider range when a frame outgrows it).
+ * Without such a fit, or with the environment variable
+ * QTL_DSF_REBUILD=callback, build is called at every displacement.
  *   modes[n_modes]   a_k on the full space (n x n, n <= 1024), 1 <= n_modes <= 16
  *   alpha0, psi0     initial coherences and ket (n entries, in the frame of alpha0)
  *   ntraj, seed      trajectories 0..ntraj-1 of the Philox streams of seed

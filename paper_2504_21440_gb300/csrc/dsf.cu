@@ -797,6 +797,12 @@ extern "C" qtl_status qtl_dsf_mcsolve(qtl_dsf_build_fn build, void* user, int32_
                 union_pattern(ss, 1, F.pC);
                 union_pattern(ss, 2, F.pO);
                 const size_t w = (size_t)F.nnz(), nA = (size_t)F.pA.nnz(), nC = (size_t)F.pC.nnz();
+                // no entries, or a fit too large for the host (M x w complex
+                // coefficients above 5e7): the callback path
+                if (w == 0 || (size_t)M * w > (size_t)50000000) {
+                    cleanup();
+                    return false;
+                }
                 auto fill = [&](const System& sy, cd* row) {
                     return values_on(sy, 0, F.pA, row) && values_on(sy, 1, F.pC, row + nA) &&
                            values_on(sy, 2, F.pO, row + nA + nC);
