@@ -522,12 +522,17 @@ qtl_status qtl_dsf_mcsolve(qtl_dsf_build_fn build, void* user, int32_t n_modes, 
  * each admitted request runs on its own CUDA stream, so requests that arrive
  * while others are on the GPU are admitted as memory frees up and their
  * kernels overlap.  A request whose kernel occupies every SM (mesolve on the
- * grid kernel, mcsolve above n = 1024) runs alone.  Submit builds the
- * system's device structures for the request (on the caller's thread) before
- * queueing it.  Results are those of the corresponding qtl_mesolve /
- * qtl_mcsolve call, bit for bit (each solve's arithmetic depends only on its
- * own inputs).  The caller's host buffers (state0, tlist, expect_out) must
- * stay valid until the request is done; the system must outlive it. */
+ * grid kernel, mcsolve above n = 1024) runs alone.  Continuous batching:
+ * a mesolve request on the cluster kernel (automatic engine and cluster size,
+ * no FP64 shadow) runs through qtl_mesolve_batch_async, and queued requests
+ * with the same output times and options join its launch (up to 64).  Submit
+ * builds the system's device structures for the request (on the caller's
+ * thread) before queueing it.  Results are bit for bit those of the
+ * corresponding call alone: qtl_mcsolve, qtl_mesolve, or for a batched
+ * mesolve qtl_mesolve with opts->cluster_size set to its batch plan's
+ * cluster size (each solve's arithmetic depends only on its own inputs).
+ * The caller's host buffers (state0, tlist, expect_out) must stay valid
+ * until the request is done; the system must outlive it. */
 typedef struct qtl_server qtl_server;
 
 enum { QTL_REQ_MESOLVE = 0, QTL_REQ_MCSOLVE = 1 };

@@ -42,7 +42,9 @@ struct SrvReq {
     size_t ex_bytes = 0;
     int state = 0;  // 0 queued, 1 running, 2 done
     int fills_gpu = 0;  // runs alone: its kernel occupies every SM
+    int batch = 0;      // a cluster-kernel mesolve: runs through the batched launch
     int slot = -1;
+    size_t stage_off = 0;  // its [info | expect] in the slot's pinned staging
     qtl_result res{};
 };
 
@@ -51,7 +53,9 @@ struct SrvSlot {
     cudaEvent_t done = nullptr;
     void* pinned = nullptr;   // staging: device info, then the expectation values
     size_t pinned_bytes = 0;
-    SrvReq* req = nullptr;
+    SrvReq* req = nullptr;            // a request run alone, or
+    std::vector<SrvReq*> group;       // requests sharing one batched launch
+    bool busy() const { return req || !group.empty(); }
 };
 
 }  // namespace qtl
@@ -202,8 +206,124 @@ static void srv_admit(qtl_server* S, SrvReq* q, int slot) {
     cudaEventRecord(sl.done, st);
 }
 
+// Requests that may share one batched launch: mesolve on the cluster kernel
+// with the same output times and options.  The batched launch gives each
+// solve the plan its own size implies (qtl_mesolve_batch), so a request's
+// result is the same bit for bit whether it runs in a group or alone.
+static bool batch_compatible(const qtl_request& a, const qtl_request& b) {
+    const qtl_opts &x = a.opts, &y = b.opts;
+    if (a.nt != b.nt || x.method != y.method || x.precision != y.precision || x.rtol != y.rtol ||
+        x.atol != y.atol || x.dt0 != y.dt0 || x.dt_min != y.dt_min || x.max_steps != y.max_steps ||
+        x.fixed_step != y.fixed_step || (x.fixed_step && x.dt_fixed != y.dt_fixed))
+        return false;
+    return std::memcmp(a.tlist, b.tlist, (size_t)a.nt * sizeof(double)) == 0;
+}
+
+constexpr int SRV_MAX_GROUP = 64;
+
+static void srv_admit_group(qtl_server* S, const std::vector<SrvReq*>& g, int slot) {
+    SrvSlot& sl = S->slots[slot];
+    cudaStream_t st = sl.stream;
+    const int nb = (int)g.size();
+    const SrvReq* q0 = g[0];
+    const size_t nt = (size_t)q0->r.nt;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // pinned staging: [info | expect] per request; device: tlist, states, expects, infos
+    size_t pin = 0, dev = up(nt * 8);
+    std::vector<size_t> o_st(nb), o_ex(nb);
+    for (int i = 0; i < nb; ++i) {
+        SrvReq* q = g[i];
+        const System& s = q->r.sys->s;
+        const size_t n0 = q->r.is_ket ? (size_t)s.n : (size_t)s.n * s.n;
+        q->ex_bytes = (size_t)s.n_e * nt * 16;
+        q->slot = slot;
+        q->state = 1;
+        q->res.t_start = now_s();
+        q->stage_off = pin;
+        pin += 64 + ((q->ex_bytes + 63) & ~(size_t)63);
+        o_st[i] = dev;
+        dev += up(n0 * 16);
+        o_ex[i] = dev;
+        dev += up(q->ex_bytes + 16);
+    }
+    const size_t o_inf = dev;
+    dev += up((size_t)nb * sizeof(qtl_device_info));
+    sl.group = g;
+    qtl_status stt = QTL_OK;
+    if (sl.pinned_bytes < pin) {
+        if (sl.pinned) cudaFreeHost(sl.pinned);
+        sl.pinned = nullptr;
+        sl.pinned_bytes = 0;
+        if (cudaMallocHost(&sl.pinned, pin) == cudaSuccess) sl.pinned_bytes = pin;
+        else stt = QTL_ENOMEM;
+    }
+    char* dbuf = nullptr;
+    if (stt == QTL_OK && qtl_malloc_async((void**)&dbuf, dev, st) != cudaSuccess) stt = QTL_ENOMEM;
+    if (stt == QTL_OK) {
+        cudaMemcpyAsync(dbuf, q0->r.tlist, nt * 8, cudaMemcpyHostToDevice, st);
+        std::vector<qtl_system*> sys(nb);
+        std::vector<const qtl_c128*> s0(nb);
+        std::vector<qtl_c128*> ex(nb);
+        std::vector<int32_t> ket(nb);
+        for (int i = 0; i < nb; ++i) {
+            const SrvReq* q = g[i];
+            const System& s = q->r.sys->s;
+            const size_t n0 = q->r.is_ket ? (size_t)s.n : (size_t)s.n * s.n;
+            cudaMemcpyAsync(dbuf + o_st[i], q->r.state0, n0 * 16, cudaMemcpyHostToDevice, st);
+            sys[i] = q->r.sys;
+            s0[i] = (const qtl_c128*)(dbuf + o_st[i]);
+            ex[i] = (qtl_c128*)(dbuf + o_ex[i]);
+            ket[i] = q->r.is_ket;
+        }
+        qtl_opts o = q0->r.opts;
+        o.cuda_stream = st;
+        qtl_device_info* dinfo = (qtl_device_info*)(dbuf + o_inf);
+        stt = qtl_mesolve_batch_async(sys.data(), nb, s0.data(), ket.data(), (const double*)dbuf, (int32_t)nt,
+                                      &o, ex.data(), dinfo);
+        if (stt == QTL_OK)
+            for (int i = 0; i < nb; ++i) {
+                char* p = (char*)sl.pinned + g[i]->stage_off;
+                cudaMemcpyAsync(p, dinfo + i, sizeof(qtl_device_info), cudaMemcpyDeviceToHost, st);
+                if (g[i]->ex_bytes)
+                    cudaMemcpyAsync(p + 64, dbuf + o_ex[i], g[i]->ex_bytes, cudaMemcpyDeviceToHost, st);
+            }
+        cudaFreeAsync(dbuf, st);
+    }
+    if (stt != QTL_OK)
+        for (SrvReq* q : g) {
+            qtl_device_info fail{};
+            fail.status = stt;
+            if (sl.pinned) std::memcpy((char*)sl.pinned + q->stage_off, &fail, sizeof(fail));
+            q->res.status = stt;
+        }
+    cudaEventRecord(sl.done, st);
+}
+
+// one request's results from its staging area
+static void srv_finish(qtl_server* S, SrvReq* q, const char* stage) {
+    qtl_device_info info{};
+    if (stage) std::memcpy(&info, stage, sizeof(info));
+    if (q->res.status == QTL_OK || q->res.status == QTL_EBUSY) q->res.status = info.status;
+    q->res.stats.steps_acc = info.steps_acc;
+    q->res.stats.steps_rej = info.steps_rej;
+    q->res.stats.rhs_evals = info.rhs_evals;
+    q->res.stats.jumps = info.jumps;
+    q->res.stats.err_vs_fp64 = q->r.opts.precision == QTL_FP64 ? 0.0 : -1.0;
+    if (q->ex_bytes && q->res.status == QTL_OK && q->expect_out && stage)
+        std::memcpy(q->expect_out, stage + 64, q->ex_bytes);
+    q->res.t_end = now_s();
+    q->state = 2;
+    S->in_use -= q->bytes;
+}
+
 static void srv_retire(qtl_server* S, int slot) {
     SrvSlot& sl = S->slots[slot];
+    if (!sl.group.empty()) {
+        for (SrvReq* q : sl.group) srv_finish(S, q, sl.pinned ? (const char*)sl.pinned + q->stage_off : nullptr);
+        S->running -= (int)sl.group.size();
+        sl.group.clear();
+        return;
+    }
     SrvReq* q = sl.req;
     qtl_device_info info{};
     if (sl.pinned) std::memcpy(&info, sl.pinned, sizeof(info));
@@ -243,7 +363,7 @@ static void srv_loop(qtl_server* S) {
     for (;;) {
         bool progressed = false;
         for (size_t i = 0; i < S->slots.size(); ++i) {
-            if (S->slots[i].req && cudaEventQuery(S->slots[i].done) == cudaSuccess) {
+            if (S->slots[i].busy() && cudaEventQuery(S->slots[i].done) == cudaSuccess) {
                 srv_retire(S, (int)i);
                 progressed = true;
             }
@@ -260,7 +380,7 @@ static void srv_loop(qtl_server* S) {
             if (S->exclusive || (q->fills_gpu && S->running > 0)) break;
             int slot = -1;
             for (size_t i = 0; i < S->slots.size(); ++i)
-                if (!S->slots[i].req) {
+                if (!S->slots[i].busy()) {
                     slot = (int)i;
                     break;
                 }
@@ -268,6 +388,24 @@ static void srv_loop(qtl_server* S) {
             S->queue.pop_front();
             S->in_use += q->bytes;
             S->running += 1;
+            if (q->batch) {
+                // continuous batching: queued requests that can share the
+                // launch join it, in queue order, while memory allows
+                std::vector<SrvReq*> g{q};
+                for (auto it = S->queue.begin(); it != S->queue.end() && (int)g.size() < SRV_MAX_GROUP;) {
+                    SrvReq* o = S->reqs[*it];
+                    if (o->batch && batch_compatible(q->r, o->r) && S->in_use + o->bytes <= S->budget) {
+                        S->in_use += o->bytes;
+                        S->running += 1;
+                        g.push_back(o);
+                        it = S->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+                srv_admit_group(S, g, slot);
+                continue;
+            }
             if (q->fills_gpu) S->exclusive = 1;
             srv_admit(S, q, slot);
         }
@@ -339,6 +477,18 @@ qtl_status qtl_server_submit(qtl_server* S, const qtl_request* req, qtl_c128* ex
     }
     SrvReq* q = new SrvReq();
     q->fills_gpu = fills;
+    // a mesolve the batched cluster launch takes (automatic engine and
+    // cluster size, no FP64 shadow, its batch plan within shared memory)
+    if (req->kind == QTL_REQ_MESOLVE && !fills && !wants_shadow(*req) && req->opts.engine == QTL_ENGINE_AUTO &&
+        req->opts.cluster_size == 0) {
+        const System& s = req->sys->s;
+        const int64_t L = (int64_t)s.n * s.n;
+        if (L <= me_cluster_capacity()) {
+            int C = 0, rpt = 0;
+            batch_plan((int)L, &C, &rpt);
+            q->batch = cta_nnz_max(s, C) <= me_smem_nnz_budget(req->opts.precision, rpt);
+        }
+    }
     q->r = *req;
     q->expect_out = expect_out;
     q->bytes = request_bytes(*req);

@@ -23,9 +23,20 @@ def _requests(qtl):
     return reqs
 
 
+def _batch_c(n):
+    """The batch plan's cluster size: the smallest C in {1, 2, 4, 8, 16} with
+    C * 1024 >= n^2 (cluster-kernel mesolve requests are served through the
+    batched launch)."""
+    for c in (1, 2, 4, 8, 16):
+        if c * 1024 >= n * n:
+            return c
+    return 0
+
+
 def _alone(qtl, kind, g, s, tol, ntraj, seed):
     if kind == "mesolve":
-        return g.mesolve(s.psi0, s.tlist, **tol)["expect"]
+        c = _batch_c(s.H.shape[0])
+        return g.mesolve(s.psi0, s.tlist, cluster_size=c, **tol)["expect"]
     return g.mcsolve(s.psi0, s.tlist, ntraj, seed, **tol)["expect"]
 
 
@@ -45,6 +56,33 @@ def test_results_in_the_mix_equal_results_alone(budget, inflight):
         alone = _alone(qtl, k, g, s, tol, nt, sd)
         assert maxabs(r["expect"], alone) == 0.0
     for g in systems:
+        g.free()
+
+
+def test_continuous_batching_groups_queued_mesolve_requests():
+    """Twelve small mesolve requests with one tlist and one set of options,
+    submitted while a slow request holds the only slot: they share launches
+    (fewer launches than requests), and each result is the solve alone."""
+    qtl = require_gpu()
+    slow = W.jaynes_cummings(N=6, nt=201, t_end=300.0)
+    gs = qtl.System(slow.H, slow.c_ops, slow.e_ops)
+    cav = [W.coupled_cavities(n1, n2, J=0.2 + 0.05 * i, kappa1=0.05, kappa2=0.1, t_end=10.0, nt=21)
+           for i, (n1, n2) in enumerate([(3, 4), (4, 4), (5, 3), (6, 5), (3, 3), (4, 6)] * 2)]
+    systems = [qtl.System(s.H, s.c_ops, s.e_ops) for s in cav]
+    tol = dict(precision="mixed", rtol=1e-7, atol=1e-9)
+    srv = qtl.Server(hbm_budget_bytes=0, max_inflight=1)
+    t_slow = srv.submit("mcsolve", gs, slow.psi0, slow.tlist, qtl.make_opts(), ntraj=2000, seed=3)
+    l0 = qtl.launch_count()
+    tickets = [srv.submit("mesolve", g, s.psi0, s.tlist, qtl.make_opts(**tol)) for g, s in zip(systems, cav)]
+    results = [srv.wait(t) for t in tickets]
+    l1 = qtl.launch_count()
+    assert srv.wait(t_slow)["status"] == 0
+    srv.free()
+    assert l1 - l0 < len(cav)
+    for s, g, r in zip(cav, systems, results):
+        assert r["status"] == 0
+        assert maxabs(r["expect"], _alone(qtl, "mesolve", g, s, tol, 0, 0)) == 0.0
+    for g in systems + [gs]:
         g.free()
 
 
