@@ -15,7 +15,10 @@ ones the CUDA library implements):
   * output times: each step is clamped so that it lands exactly on the next
     time of tlist (no interpolation); a step that would stop short of that
     time by no more than LAND_ULPS units of 2^-52 max(1, |t_target|) lands
-    on it instead, so that rounding in t never leaves a vanishing remnant.
+    on it instead, so that rounding in t never leaves a vanishing remnant;
+    with adaptive steps, a step that would cover more than half of the rest
+    of the way, but not all of it, is shortened to half of it, so that two
+    equal steps land rather than a full step and a short remainder.
 """
 import math
 
@@ -126,7 +129,7 @@ def initial_step(f, t0, y0, f0, rtol, atol):
 
 def integrate(f, y0, tlist, tab, rtol, atol, on_save, dt0=0.0, fixed_dt=None,
               max_steps=10_000_000, dt_min=0.0, after_accept=None, stats=None,
-              beta1=BETA1, beta2=BETA2):
+              beta1=BETA1, beta2=BETA2, balance=True):
     """Integrate y' = f(t, y) from tlist[0], calling on_save(idx, t, y) at
     every tlist point (steps land on them exactly).
 
@@ -134,7 +137,11 @@ def integrate(f, y0, tlist, tab, rtol, atol, on_save, dt0=0.0, fixed_dt=None,
     tlist point) and is accepted without error control.
     after_accept(t, y, k1, h, t_new, y_new, k_last) may return a replacement
     (t, y, k1) to restart from (used by the quantum-jump method).
-    beta1, beta2: the step controller's exponents (PIController)."""
+    beta1, beta2: the step controller's exponents (PIController).
+    balance: with adaptive steps, when the proposed step covers more than
+    half of the way to the next tlist point without reaching it, the step
+    is half of the way, so that two equal steps land (reading G7); False
+    gives the plain clamp of the last step (the SciPy pin)."""
     st = stats if stats is not None else Stats()
     t = float(tlist[0])
     y = np.array(y0, dtype=np.complex128)
@@ -156,8 +163,14 @@ def integrate(f, y0, tlist, tab, rtol, atol, on_save, dt0=0.0, fixed_dt=None,
             if nsteps >= max_steps:
                 raise StepLimitError("max_steps reached")
             nsteps += 1
-            land = h >= (t_target - t) - LAND_ULPS * 2.0 ** -52 * max(1.0, abs(t_target))
-            h_try = (t_target - t) if land else h
+            rem = t_target - t
+            land = h >= rem - LAND_ULPS * 2.0 ** -52 * max(1.0, abs(t_target))
+            if land:
+                h_try = rem
+            elif balance and fixed_dt is None and h >= 0.5 * rem:
+                h_try = 0.5 * rem      # two equal steps land (reading G7)
+            else:
+                h_try = h
             y_new, ks = rk_step(f, t, y, h_try, k1, tab)
             st.rhs_evals += tab.stages - 1
             if fixed_dt is None:

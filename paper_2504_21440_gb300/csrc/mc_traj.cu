@@ -295,8 +295,8 @@ __global__ void __launch_bounds__(MAXT, MINB) mc_traj_kernel(McJob J) {
                     continue;
                 }
                 ++attempts;
-                const bool land = lands(h, t, t_target);
-                htry = land ? (t_target - t) : h;
+                bool land;
+                htry = step_toward(h, t, t_target, J.fixed != 0, &land);
                 cb.land = land;
                 cb.action = MC_STEP;
                 cb.coef[27] = htry;

@@ -692,8 +692,8 @@ __global__ void __launch_bounds__(MW_T, 1) mc_wide_kernel(McJob J, const __grid_
                     continue;
                 }
                 ++attempts;
-                const bool land = lands(h, t, t_target);
-                htry = land ? (t_target - t) : h;
+                bool land;
+                htry = step_toward(h, t, t_target, J.fixed != 0, &land);
                 cb.land = land;
                 cb.action = MC_STEP;
                 cb.coef[27] = htry;

@@ -614,8 +614,8 @@ __device__ void me_solve(const MeJob& J, MeShared& sh, cg::cluster_group& cl, un
                 continue;
             }
             ++attempts;
-            const bool land = lands(h, t, t_target);
-            htry = land ? (t_target - t) : h;
+            bool land;
+            htry = step_toward(h, t, t_target, J.fixed != 0, &land);
             sh.land = land;
             sh.action = ACT_STEP;
             sh.coef[27] = htry;  // handed to warp 0 for the coefficient products

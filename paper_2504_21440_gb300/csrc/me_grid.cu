@@ -850,8 +850,8 @@ __global__ void __launch_bounds__(MG_T, MIXED ? 2 : 1) me_grid_kernel(MgJob J) {
                 continue;
             }
             ++attempts;
-            const bool land = lands(h, t, t_target);
-            htry = land ? (t_target - t) : h;
+            bool land;
+            htry = step_toward(h, t, t_target, J.fixed != 0, &land);
             sh.land = land;
             sh.refresh_now = MIXED && z.since_refresh + 1 >= J.refresh;
             sh.action = MG_STEP;

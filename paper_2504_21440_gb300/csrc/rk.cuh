@@ -105,6 +105,19 @@ __device__ __forceinline__ bool lands(double h, double t, double t_target) {
     return h >= (t_target - t) - 64.0 * 0x1p-52 * fmax(1.0, fabs(t_target));
 }
 
+// The step to try toward the next output time t_target from t, with the
+// controller's step h: the rest of the way when h lands on it; with adaptive
+// steps, half the rest when h covers more than half of it, so that two equal
+// steps land instead of a full step and a short remainder (whose small size
+// the controller would then have to grow back); else h.
+__device__ __forceinline__ double step_toward(double h, double t, double t_target, bool fixed, bool* land) {
+    const double rem = t_target - t;
+    *land = lands(h, t, t_target);
+    if (*land) return rem;
+    if (!fixed && h >= 0.5 * rem) return 0.5 * rem;
+    return h;
+}
+
 // Starting step of Hairer, Norsett & Wanner (Solving ODEs I, Sec. II.4) for a
 // method of order 5, from the RMS norms d0 = |y0|, d1 = |f0|, d2 = |f1-f0|/h0.
 __device__ __forceinline__ double start_h0(double d0, double d1) {

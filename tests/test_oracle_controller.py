@@ -38,7 +38,7 @@ def _oracle_steps(f, y0, t0, t1, rtol, atol):
         return None
 
     st = integrate(f, y0, np.array([t0, t1]), DP5, rtol, atol, lambda *a: None,
-                   after_accept=after, beta1=0.2, beta2=0.0)
+                   after_accept=after, beta1=0.2, beta2=0.0, balance=False)
     return np.array(times), st
 
 
@@ -188,3 +188,41 @@ def test_planted_controller_mistakes_break_the_pin(plant, monkeypatch):
         if len(ours) != len(ref) or st.rhs_evals != nfev or np.max(np.abs(ours - ref)) > 1e-9 * t1:
             broken = True
     assert broken
+
+
+def test_balanced_landing_takes_two_equal_steps():
+    """With adaptive steps and output times denser than the free step size
+    allows, a step that would cover more than half of the way to an output
+    time without reaching it is cut to half of it, and the next step lands:
+    every landing step equals the step before it whenever that step was
+    balanced, no landing step is shorter than half the free step before it,
+    and the balanced solve takes fewer steps than the plain clamp to the same
+    accuracy (y' = (-0.3 + 2i) y, exact solution)."""
+    lam = -0.3 + 2.0j
+    f = lambda t, y: lam * y
+    y0 = np.array([1.0 + 0.0j])
+    tl = np.linspace(0.0, 10.0, 41)
+    res = {}
+    for bal in (False, True):
+        steps, vals = [], {}
+
+        def after(t, y, k1, h, t_new, y_new, k_last, steps=steps):
+            steps.append((t, t_new))
+            return None
+
+        st = integrate(f, y0, tl, DP5, 1e-9, 1e-12, lambda i, t, y, vals=vals: vals.__setitem__(i, y[0]),
+                       after_accept=after, balance=bal)
+        got = np.array([vals[i] for i in range(len(tl))])
+        assert np.max(np.abs(got - np.exp(lam * tl))) <= 1e-7
+        res[bal] = (st, steps)
+    (st0, s0), (st1, s1) = res[False], res[True]
+    assert st1.steps_acc < st0.steps_acc
+    grid = set(np.round(tl, 12))
+    seen = 0
+    for (ta, tb), (tc, td) in zip(s1, s1[1:]):
+        if round(td, 12) in grid and round(tb, 12) not in grid:
+            h_prev, h_land = tb - ta, td - tc
+            assert h_land >= 0.5 * h_prev * (1 - 1e-12)
+            if abs(h_land - h_prev) <= 1e-12 * h_prev:
+                seen += 1
+    assert seen > 5
