@@ -5,6 +5,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -28,3 +30,14 @@ def test_reference_arm_refuses_other_workloads():
 def test_single_gpu_workloads_refuse_torchrun():
     r = _run(["--workload", "smesolve_jc", "--gpus", "2"], RANK="0", LOCAL_RANK="0", WORLD_SIZE="2")
     assert r.returncode != 0 and "one GPU" in r.stderr
+
+
+@pytest.mark.parametrize("workload", ["steadystate", "dsf", "dsf_mc"])
+def test_newer_workloads_are_accepted_and_routed(workload):
+    """The stationary-state and DSF workloads parse, refuse torchrun (one
+    GPU each) and refuse the reference arm (their lines carry the oracle's
+    timing in cpu_baseline)."""
+    r = _run(["--workload", workload, "--gpus", "2"], RANK="0", LOCAL_RANK="0", WORLD_SIZE="2")
+    assert r.returncode != 0 and "one GPU" in r.stderr
+    r = _run(["--impl", "reference", "--workload", workload])
+    assert r.returncode != 0 and "cpu_baseline" in r.stderr
