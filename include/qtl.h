@@ -199,7 +199,8 @@ typedef struct {
  * plans.  Mixed-precision mesolve on the grid kernel returns QTL_EINVAL for
  * such a system.
  * Errors: QTL_EINVAL (NULL, bad operator or coefficient, 8 terms already,
- * a solve already ran), QTL_ENOMEM, QTL_ECUDA. */
+ * a solve already ran or a request on the system was submitted to a
+ * server), QTL_ENOMEM (the system keeps its earlier terms), QTL_ECUDA. */
 qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* f);
 
 /* Releases the system and its device memory (NULL is a no-op).  Work enqueued

@@ -244,6 +244,17 @@ static qtl_status upload(T** dst, const T* src, size_t count) {
     return QTL_OK;
 }
 
+static void free_csr(DevCsr& d) {
+    cudaFree(d.seg);
+    cudaFree(d.rp);
+    cudaFree(d.ci);
+    cudaFree(d.v64);
+    cudaFree(d.v32);
+    d = DevCsr();
+}
+
+// All or nothing: on failure nothing stays allocated and d is empty, so a
+// non-null d.rp always means a complete upload.
 static qtl_status upload_csr(const Csr& m, DevCsr& d) {
     d.n = m.n;
     d.nnz = m.nnz();
@@ -279,21 +290,13 @@ static qtl_status upload_csr(const Csr& m, DevCsr& d) {
         seg[r] = make_int4(b[0], b[1], b[2], m.rp[r + 1]);
     }
     qtl_status st;
-    if ((st = upload(&d.seg, seg.data(), seg.size())) != QTL_OK) return st;
-    if ((st = upload(&d.rp, m.rp.data(), m.rp.size())) != QTL_OK) return st;
-    if ((st = upload(&d.ci, ci.data(), ci.size())) != QTL_OK) return st;
-    if ((st = upload(&d.v64, v64.data(), v64.size())) != QTL_OK) return st;
-    if ((st = upload(&d.v32, v32.data(), v32.size())) != QTL_OK) return st;
-    return QTL_OK;
-}
-
-static void free_csr(DevCsr& d) {
-    cudaFree(d.seg);
-    cudaFree(d.rp);
-    cudaFree(d.ci);
-    cudaFree(d.v64);
-    cudaFree(d.v32);
-    d = DevCsr();
+    if ((st = upload(&d.seg, seg.data(), seg.size())) != QTL_OK ||
+        (st = upload(&d.rp, m.rp.data(), m.rp.size())) != QTL_OK ||
+        (st = upload(&d.ci, ci.data(), ci.size())) != QTL_OK ||
+        (st = upload(&d.v64, v64.data(), v64.size())) != QTL_OK ||
+        (st = upload(&d.v32, v32.data(), v32.size())) != QTL_OK)
+        free_csr(d);
+    return st;
 }
 
 qtl_status op_to_csr(const qtl_op* op, int n_expect, Csr& out) { return to_csr(op, n_expect, out); }
@@ -566,29 +569,27 @@ static bool exactly_hermitian(const Csr& m) {
 // The caller holds g_build_mu.
 static qtl_status ensure_td_sell_locked(System& s) {
     if (s.Htd.empty() || s.d_tsl) return QTL_OK;
-    qtl_status st;
-    {
-        const int ntd = (int)s.Htd.size();
-        s.sTa.resize(ntd);
-        s.sTb.resize(ntd);
-        std::vector<SellRef> refs(2 * ntd);
-        for (int k = 0; k < ntd; ++k) {
-            const Csr& h = s.Htd[k];
-            Csr ta = h, tb;
-            for (int64_t p = 0; p < ta.nnz(); ++p) {   // -i (re + i im) = im - i re
-                const double re = h.re[p], im = h.im[p];
-                ta.re[p] = im;
-                ta.im[p] = -re;
-            }
-            // (i H)^T: row j holds i H[i][j] at column i
-            std::vector<std::vector<std::pair<int32_t, cplx>>> rows(s.n);
-            for (int i = 0; i < s.n; ++i)
-                for (int64_t p = h.rp[i]; p < h.rp[i + 1]; ++p)
-                    rows[h.ci[p]].emplace_back(i, cplx(-h.im[p], h.re[p]));
-            rows_to_csr(s.n, rows, tb);
-            if ((st = upload_sell(ta, s.sTa[k])) != QTL_OK || (st = upload_sell(tb, s.sTb[k])) != QTL_OK)
-                return st;
+    const int ntd = (int)s.Htd.size();
+    s.sTa.resize(ntd);
+    s.sTb.resize(ntd);
+    qtl_status st = QTL_OK;
+    for (int k = 0; k < ntd && st == QTL_OK; ++k) {
+        const Csr& h = s.Htd[k];
+        Csr ta = h, tb;
+        for (int64_t p = 0; p < ta.nnz(); ++p) {   // -i (re + i im) = im - i re
+            const double re = h.re[p], im = h.im[p];
+            ta.re[p] = im;
+            ta.im[p] = -re;
         }
+        // (i H)^T: row j holds i H[i][j] at column i
+        std::vector<std::vector<std::pair<int32_t, cplx>>> rows(s.n);
+        for (int i = 0; i < s.n; ++i)
+            for (int64_t p = h.rp[i]; p < h.rp[i + 1]; ++p)
+                rows[h.ci[p]].emplace_back(i, cplx(-h.im[p], h.re[p]));
+        rows_to_csr(s.n, rows, tb);
+        if ((st = upload_sell(ta, s.sTa[k])) == QTL_OK) st = upload_sell(tb, s.sTb[k]);
+    }
+    if (st == QTL_OK) {
         auto ref = [](const DevSell& d) {
             SellRef r;
             r.sl = d.sl;
@@ -600,13 +601,23 @@ static qtl_status ensure_td_sell_locked(System& s) {
             r.vc32 = d.vc32;
             return r;
         };
+        std::vector<SellRef> refs(2 * ntd);
         for (int k = 0; k < ntd; ++k) {
             refs[k] = ref(s.sTa[k]);
             refs[ntd + k] = ref(s.sTb[k]);
         }
-        if ((st = upload(&s.d_tsl, refs.data(), refs.size())) != QTL_OK) return st;
+        st = upload(&s.d_tsl, refs.data(), refs.size());
     }
-    return QTL_OK;
+    if (st != QTL_OK) {
+        // all or nothing: a later call starts again from empty tables
+        for (DevSell& d : s.sTa) free_sell(d);
+        for (DevSell& d : s.sTb) free_sell(d);
+        s.sTa.clear();
+        s.sTb.clear();
+        cudaFree(s.d_tsl);
+        s.d_tsl = nullptr;
+    }
+    return st;
 }
 
 qtl_status ensure_td_sell(System& s) {
@@ -623,11 +634,20 @@ static qtl_status ensure_grid(System& s) {
     qtl_status st = ensure_sell(s);
     if (st != QTL_OK) return st;
     std::lock_guard<std::mutex> lk(g_build_mu);
-    if (s.units) return QTL_OK;
-    if ((st = upload_sell(s.Bt, s.sBt)) != QTL_OK) {
+    if (s.units) return QTL_OK;   // the work units are uploaded last: present means complete
+    if (!s.sBt.sl && (st = upload_sell(s.Bt, s.sBt)) != QTL_OK) {
         free_sell(s.sBt);
         return st;
     }
+    if ((st = ensure_td_sell_locked(s)) != QTL_OK) return st;
+    bool herm = exactly_hermitian(s.H);
+    for (size_t k = 0; k < s.Htd.size(); ++k)
+        herm = herm && s.ftd[k].kind == QTL_COEF_COS && s.ftd[k].amp_im == 0.0 && exactly_hermitian(s.Htd[k]);
+    s.herm_h = herm ? 1 : 0;
+    bool real = true;
+    for (const Csr& c : s.C)
+        for (double v : c.im) real = real && v == 0.0;
+    s.c_real = real ? 1 : 0;
     const int n = s.n, ns = (n + 31) / 32, ncg = (n + 3) / 4;
     std::vector<int2> lower, upper;
     for (int c = 0; c < ncg; ++c)
@@ -638,17 +658,7 @@ static qtl_status ensure_grid(System& s) {
     s.nu_tri = (int)lower.size();
     s.nu_all = (int)(lower.size() + upper.size());
     lower.insert(lower.end(), upper.begin(), upper.end());
-    if ((st = upload(&s.units, lower.data(), lower.size())) != QTL_OK) return st;
-    bool herm = exactly_hermitian(s.H);
-    for (size_t k = 0; k < s.Htd.size(); ++k)
-        herm = herm && s.ftd[k].kind == QTL_COEF_COS && s.ftd[k].amp_im == 0.0 && exactly_hermitian(s.Htd[k]);
-    s.herm_h = herm ? 1 : 0;
-    if ((st = ensure_td_sell_locked(s)) != QTL_OK) return st;
-    bool real = true;
-    for (const Csr& c : s.C)
-        for (double v : c.im) real = real && v == 0.0;
-    s.c_real = real ? 1 : 0;
-    return QTL_OK;
+    return upload(&s.units, lower.data(), lower.size());
 }
 
 // The Liouvillians of the time-dependent terms alone, L_k = -i (I kron H_k -
@@ -703,6 +713,7 @@ qtl_status ensure_liouvillian(System& s, int64_t max_rows) {
                 for (int64_t p = o.rp[i]; p < o.rp[i + 1]; ++p)
                     ew[((size_t)o.ci[p] + (size_t)s.n * i) * s.n_e + e] = make_double2(o.re[p], o.im[p]);
         }
+        cudaFree(s.ew);   // left by an earlier attempt whose Liouvillian upload failed
         qtl_status st = upload(&s.ew, ew.data(), ew.size());
         if (st != QTL_OK) return st;
     }
@@ -767,6 +778,7 @@ int64_t cta_nnz_max_of(const System& s, int C) {
 // The choice of engine repeats the one the solve makes.
 qtl_status prepare_solve(System& s, int kind, const qtl_opts* o, int* fills_gpu) {
     if (fills_gpu) *fills_gpu = 0;
+    s.solved = true;   // the structures built here hold the terms as they are now
     if (kind == QTL_REQ_MCSOLVE) {
         const bool wide = s.n > mc_traj_capacity() || o->engine == QTL_ENGINE_GRID;
         if (fills_gpu) *fills_gpu = wide;
@@ -1129,14 +1141,19 @@ qtl_status qtl_system_add_td(qtl_system* sys, const qtl_op* Hk, const qtl_coef* 
     }
     Csr stacked;
     stack(scaled, s.n, stacked);
-    free_csr(s.dT);
-    cudaFree(s.d_tf);
-    s.d_tf = nullptr;
-    if ((st = upload_csr(stacked, s.dT)) != QTL_OK || (st = upload(&s.d_tf, s.ftd.data(), s.ftd.size())) != QTL_OK) {
+    // the earlier terms keep their device copies unless the new ones are complete
+    DevCsr nT;
+    decltype(s.d_tf) ntf = nullptr;
+    if ((st = upload_csr(stacked, nT)) != QTL_OK || (st = upload(&ntf, s.ftd.data(), s.ftd.size())) != QTL_OK) {
+        free_csr(nT);
         s.Htd.pop_back();
         s.ftd.pop_back();
         return st;
     }
+    free_csr(s.dT);
+    cudaFree(s.d_tf);
+    s.dT = nT;
+    s.d_tf = ntf;
     return QTL_OK;
 }
 

@@ -108,6 +108,27 @@ def test_budget_refusal_and_cancel():
     g.free()
 
 
+def test_terms_are_frozen_once_a_request_is_submitted():
+    """A submit builds the system's device structures from its terms as they
+    are, so a time-dependent term added afterwards is refused and the served
+    result is that of the system as submitted."""
+    qtl = require_gpu()
+    s = W.jaynes_cummings(N=6, nt=11, t_end=5.0)
+    g = qtl.System(s.H, s.c_ops, s.e_ops)
+    srv = qtl.Server(max_inflight=1)
+    t = srv.submit("mesolve", g, s.psi0, s.tlist, qtl.make_opts())
+    drive = s.c_ops[0] + s.c_ops[0].conj().T
+    with pytest.raises(qtl.QtlError) as e:
+        qtl.system_add_td(g.handle, drive, dict(kind="cos", amp=0.1, omega=1.0))
+    assert e.value.status == qtl.QTL_EINVAL
+    r = srv.wait(t)
+    assert r["status"] == 0
+    ref = g.mesolve(s.psi0, s.tlist, cluster_size=_batch_c(s.H.shape[0]))["expect"]
+    assert np.array_equal(r["expect"], ref)
+    srv.free()
+    g.free()
+
+
 def test_served_mixed_results_against_fp64_and_the_oracle():
     """Requests drawn from the serving mix (coupled-cavity mesolve and Ising
     mcsolve, mixed precision, each with its FP64 shadow): every mesolve
