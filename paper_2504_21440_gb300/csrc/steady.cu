@@ -27,6 +27,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -454,6 +455,9 @@ struct SsSolver {
 
 // The eigendecomposition of A = -i H_eff and its device copies, built once per system.
 static qtl_status ensure_ss_cache(System& s) {
+    // built once per system; concurrent first solves on one system build it once
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
     if (s.ss) return QTL_OK;
     const int n = s.n;
     std::vector<cd> A((size_t)n * n, 0.0), lam, V, Vi;
