@@ -132,13 +132,15 @@ def workload():
     return s
 
 
-def algorithmic_flops(nnz, n_rows, stats):
-    """FP64 flops of the integrator counted from the work done: a complex
-    multiply-add is 8 flops per stored operator entry per RHS evaluation;
+def algorithmic_flops(nnz, nnz_half, n_rows, stats):
+    """FP64 flops of the integrator counted from the work done: per RHS
+    evaluation a complex multiply-add (8 flops) per stored operator entry,
+    or 4 flops for the nnz_half entries whose real or imaginary part is zero;
     each attempted step forms 21 stage increments and 7 error terms, each a
     real-times-complex product added to a complex entry (4 flops) per row."""
     attempts = stats["steps_acc"] + stats["steps_rej"]
-    return 8.0 * nnz * stats["rhs_evals"] + 4.0 * 28 * n_rows * attempts
+    per_rhs = 8.0 * (nnz - nnz_half) + 4.0 * nnz_half
+    return per_rhs * stats["rhs_evals"] + 4.0 * 28 * n_rows * attempts
 
 
 def traffic_from_profile(kernel_src, summary):
@@ -246,6 +248,7 @@ def run_qtl(args):
         step()
         torch.cuda.synchronize(dev)
     nnz_L, nnz_A = qtl.system_nnz(g.handle, 2), qtl.system_nnz(g.handle, 1)
+    half_L, half_A = qtl.system_nnz(g.handle, 4), qtl.system_nnz(g.handle, 3)
 
     if dist is not None:
         dist.barrier()
@@ -283,8 +286,8 @@ def run_qtl(args):
     value = world * st_me_d["rhs_evals"] / (ms_per_step / 1e3)
 
     # roofline of the dominant kernel (FP64 ALU bound)
-    fl_mc = algorithmic_flops(nnz_A, s.n, st_mc_d)
-    fl_me = algorithmic_flops(nnz_L, s.n * s.n, st_me_d)
+    fl_mc = algorithmic_flops(nnz_A, half_A, s.n, st_mc_d)
+    fl_me = algorithmic_flops(nnz_L, half_L, s.n * s.n, st_me_d)
     k_me, k_mc = statistics.mean(me_ms), statistics.mean(mc_ms)
     dom = "mc_traj_kernel" if k_mc >= k_me else "me_cluster_kernel"
     fl, kms = (fl_mc, k_mc) if dom == "mc_traj_kernel" else (fl_me, k_me)

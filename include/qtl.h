@@ -214,7 +214,9 @@ int64_t qtl_system_liouvillian_nnz(const qtl_system* sys);
 
 /* Stored entries of one of the system's operators: which = 0 for H, 1 for
  * A = -i H_eff (the trajectory right-hand side), 2 for the Liouvillian (0
- * before it is built).  -1 for a NULL system or an unknown `which`. */
+ * before it is built); 3 and 4 count those of A and of the Liouvillian whose
+ * real or imaginary part is zero (a product with such an entry takes 4 flops
+ * instead of 8).  -1 for a NULL system or an unknown `which`. */
 int64_t qtl_system_nnz(const qtl_system* sys, int32_t which);
 
 /* mesolve (Sec. 3.2): integrates d rho/dt = L rho from tlist[0].

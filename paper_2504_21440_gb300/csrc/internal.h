@@ -32,6 +32,7 @@ struct DevCsr {
     int32_t* ci = nullptr;
     double2* v64 = nullptr;
     float2* v32 = nullptr;
+    int64_t nnz_half = 0;   // entries with a zero real or zero imaginary part (4 flops in a product, not 8)
 };
 
 // Sliced ELLPACK copy of A for the wide trajectory kernel, with the

@@ -258,6 +258,7 @@ static void free_csr(DevCsr& d) {
 static qtl_status upload_csr(const Csr& m, DevCsr& d) {
     d.n = m.n;
     d.nnz = m.nnz();
+    d.nnz_half = 0;
     std::vector<double2> v64(m.nnz());
     std::vector<float2> v32(m.nnz());
     std::vector<int32_t> ci(m.nnz());
@@ -288,6 +289,7 @@ static qtl_status upload_csr(const Csr& m, DevCsr& d) {
             }
         }
         seg[r] = make_int4(b[0], b[1], b[2], m.rp[r + 1]);
+        d.nnz_half += b[2] - b[0];
     }
     qtl_status st;
     if ((st = upload(&d.seg, seg.data(), seg.size())) != QTL_OK ||
@@ -1350,6 +1352,8 @@ int64_t qtl_system_nnz(const qtl_system* sys, int32_t which) {
         case 0: return sys->s.H.nnz();
         case 1: return sys->s.A.nnz();
         case 2: return sys->s.dL.nnz;
+        case 3: return sys->s.dA.nnz_half;
+        case 4: return sys->s.dL.nnz_half;
     }
     return -1;
 }

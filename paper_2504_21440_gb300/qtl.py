@@ -367,7 +367,9 @@ def system_liouvillian_nnz(sys):
 
 
 def system_nnz(sys, which):
-    """qtl_system_nnz: stored entries of H (0), A = -i H_eff (1), the Liouvillian (2)."""
+    """qtl_system_nnz: stored entries of H (0), A = -i H_eff (1), the
+    Liouvillian (2); of A (3) and the Liouvillian (4) those with a zero real or
+    imaginary part."""
     return int(load().qtl_system_nnz(sys, int(which)))
 
 

@@ -168,3 +168,31 @@ def test_async_device_path_matches_host_path():
     assert int(info[0].item() & 0xffffffff) == 0
     assert maxabs(ex.cpu().numpy(), host["expect"]) == 0.0
     g.free()
+
+
+def test_entry_type_counts_of_a_and_the_liouvillian():
+    """qtl_system_nnz's counts of entries with a zero real or imaginary part
+    (the products that take 4 flops, not 8), against their closed forms for
+    a driven damped cavity H = D a^dag a + F (a + a^dag), C = sqrt(k) a with
+    dyadic D, F, k, where every entry's real and imaginary parts are exact:
+    A = -i H - (k/2) a^dag a has N - 1 complex diagonal entries (n = 0 is
+    zero) and 2 (N - 1) imaginary off-diagonal ones; the Liouvillian has
+    N^2 - 1 diagonal entries -i D (i - j) - (k/2)(i + j), real for the N - 1
+    with i = j, (N - 1)^2 real jump entries k sqrt((i+1)(j+1)) and 4 N (N - 1)
+    imaginary drive entries."""
+    import scipy.sparse as sp
+    qtl = require_gpu()
+    N, D, F, k = 6, 0.5, 0.25, 1.0
+    a = sp.diags(np.sqrt(np.arange(1, N)), 1, format="csr", dtype=complex)
+    H = D * (a.conj().T @ a) + F * (a + a.conj().T)
+    g = qtl.System(H, [np.sqrt(k) * a], [a.conj().T @ a])
+    try:
+        assert qtl.system_nnz(g.handle, 1) == 3 * (N - 1)
+        assert qtl.system_nnz(g.handle, 3) == 2 * (N - 1)
+        psi0 = np.zeros(N, complex)
+        psi0[0] = 1.0
+        g.mesolve(psi0, np.linspace(0.0, 0.5, 3))
+        assert qtl.system_nnz(g.handle, 2) == (N * N - 1) + (N - 1) ** 2 + 4 * N * (N - 1)
+        assert qtl.system_nnz(g.handle, 4) == (N - 1) + (N - 1) ** 2 + 4 * N * (N - 1)
+    finally:
+        g.free()
