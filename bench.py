@@ -292,7 +292,7 @@ def run_qtl(args):
     dom = "mc_traj_kernel" if k_mc >= k_me else "me_cluster_kernel"
     fl, kms = (fl_mc, k_mc) if dom == "mc_traj_kernel" else (fl_me, k_me)
     achieved = fl / (kms / 1e3) / 1e12
-    src = "mc_traj.cu" if dom == "mc_traj_kernel" else "me_cluster.cu"
+    src = "mc_traj.cuh" if dom == "mc_traj_kernel" else "me_cluster.cu"
     traffic = traffic_from_profile(os.path.join(ROOT, "paper_2504_21440_gb300", "csrc", src),
                                    os.path.join(ROOT, "profiles", f"{dom}_jc40x2_fp64.md"))
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -58,7 +58,7 @@ def build(verbose=False, extra_flags=()):
         if verbose and (r.stdout or r.stderr):
             print(r.stdout + r.stderr)
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(jobs)))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 8))) as ex:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
         run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs])
